@@ -1,0 +1,205 @@
+/*
+ * svlcov.h -- C ABI of the GB300 library for updating a rank-k truncated SVD
+ * of a sparse matrix with the SV-LCOV method ("Fast Updating Truncated SVD
+ * for Representation Learning with Sparse Matrices", arXiv 2401.09703).
+ *
+ * Object maintained (Section 3.2, extended decomposition):
+ *     A_k = U' U'' Sigma V''^T V'^T,   U = U' U'' and V = V' V'' orthonormal,
+ * with U' (m x k) and V' (n x k) held in caller-owned device buffers in a
+ * storage precision (FP64, FP32 or BF16), and U'', V'' (k x k) and Sigma kept
+ * by the library in its workspace.  Each update returns the rank-k truncated
+ * SVD of the modified A_k (Section 3.3, "maintaining an approximate rank-k
+ * truncated SVD"; Theorem 1) in time proportional to the batch's nonzeros,
+ * plus an O(m k^2) reset when a small factor becomes ill-conditioned.
+ *
+ * Conventions.
+ *   - Every pointer argument named as "device" must point to GPU memory
+ *     reachable from the current device; "host" pointers to host memory.
+ *   - Dense factors are row-major: row i of U' is k contiguous elements.
+ *   - A batch of s update vectors of length d is a CSR matrix with s rows
+ *     and d columns: row j of the CSR is update vector j (for new columns
+ *     E_c (m x s) the CSR holds E_c^T; for new rows E_r it holds E_r; for a
+ *     weight update D E_m^T it holds D^T and E_m^T).  Column indices within a
+ *     row need not be sorted; duplicates are rejected.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls are
+ *     stream-ordered and asynchronous unless stated otherwise.
+ *   - Ownership: the caller owns every buffer it passes and keeps the factor
+ *     buffers and the workspace alive until svlcov_destroy.  The library
+ *     holds non-owning pointers and allocates no device memory.
+ *
+ * Errors.  Functions return SVLCOV_OK or a host-detected error synchronously
+ * (argument, capacity or CUDA launch errors; nothing is enqueued then).
+ * Errors found on the device (malformed CSR, non-finite values, ...) are
+ * OR-ed into a status word in the workspace; every kernel of a step checks it
+ * first, so a failed step and all later steps leave the factors unchanged
+ * until svlcov_status() has reported and cleared the error.
+ */
+#ifndef SVLCOV_H
+#define SVLCOV_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+/* ---- return and status codes ------------------------------------------- */
+#define SVLCOV_OK 0
+#define SVLCOV_ERR_INVALID_ARG 1 /* host: null pointer, bad shape, unsupported k or s */
+#define SVLCOV_ERR_CAPACITY 2    /* host: would exceed max_m/max_n/max_s/max_nnz or the workspace */
+#define SVLCOV_ERR_CUDA 3        /* host: a CUDA runtime call failed */
+#define SVLCOV_ERR_STATE 4       /* host: a device error is pending; call svlcov_status first */
+/* device status bits (OR-ed), reported by svlcov_status */
+#define SVLCOV_DEV_BAD_CSR 0x10   /* indptr not monotone/out of range, index out of range, duplicate */
+#define SVLCOV_DEV_NONFINITE 0x20 /* NaN/Inf in batch values or in a small-step result */
+#define SVLCOV_DEV_NOT_PD 0x40    /* residual Gram matrix E^T E - C^T C not finite */
+#define SVLCOV_DEV_GAP_WARN 0x80  /* backward: a singular-value pair fell under the gap guard */
+#define SVLCOV_DEV_TIMEOUT 0x100  /* a bounded device wait ran out */
+
+/* storage precision of U' and V' (and of the factors read back) */
+#define SVLCOV_FP64 0
+#define SVLCOV_FP32 1
+#define SVLCOV_BF16 2
+
+/* precision of the small dense steps (Gram, CholeskyQR2, Rayleigh-Ritz SVD, folds) */
+#define SVLCOV_SMALL_FP64 0  /* all small steps in native FP64 */
+#define SVLCOV_SMALL_FP32 1  /* all small steps in FP32 (the plain FP32 path) */
+#define SVLCOV_SMALL_MIXED 2 /* FP32 sweeps and factorizations with FP64 Gram/refinement */
+
+#define SVLCOV_MAX_K 128
+#define SVLCOV_MAX_S 1024
+
+typedef struct svlcov_handle svlcov_handle;
+
+/* A batch of update vectors in CSR form (all arrays on the device). */
+typedef struct {
+  int32_t rows;           /* s, number of update vectors (0 <= s <= max_s)      */
+  int32_t cols;           /* d, length of each vector                           */
+  int64_t nnz;            /* number of stored entries (= indptr[rows])          */
+  const int32_t* indptr;  /* device, rows + 1 entries, indptr[0] = 0            */
+  const int32_t* indices; /* device, nnz entries in [0, cols)                   */
+  const void* values;     /* device, nnz entries of values_dtype                */
+  int32_t values_dtype;   /* SVLCOV_FP64 or SVLCOV_FP32                         */
+} svlcov_csr;
+
+/* Everything svlcov_init needs. */
+typedef struct {
+  int64_t m, n;           /* current shape of A                                  */
+  int32_t k;              /* rank, 1 <= k <= SVLCOV_MAX_K                        */
+  int64_t max_m, max_n;   /* row capacity of ubuf / vbuf                         */
+  int32_t max_s;          /* largest batch width, <= SVLCOV_MAX_S                */
+  int64_t max_nnz;        /* largest nnz of one batch (per side)                 */
+  int32_t storage;        /* SVLCOV_FP64 / FP32 / BF16 for U', V'                */
+  int32_t small;          /* SVLCOV_SMALL_*                                      */
+  const void* U0;         /* device, m x k row-major, init_dtype: starting U     */
+  const double* sigma0;   /* device, k: starting singular values (descending)   */
+  const void* V0;         /* device, n x k row-major, init_dtype: starting V     */
+  int32_t init_dtype;     /* SVLCOV_FP64 or SVLCOV_FP32                          */
+  void* ubuf;             /* device, max_m x k of storage dtype (U')            */
+  void* vbuf;             /* device, max_n x k of storage dtype (V')            */
+  void* workspace;        /* device, >= svlcov_workspace_bytes(desc) bytes,     */
+  size_t workspace_bytes; /*   256-byte aligned                                  */
+  double tau;             /* deflation threshold (<= 0: default for `small`)     */
+  double reset_threshold; /* cond_1 bound on U'', V'' (<= 0: default for storage) */
+} svlcov_init_desc;
+
+/* Size in bytes of the device workspace that `d` needs (host only, no CUDA
+ * call).  Reads m, n, k, max_s, max_nnz, small; returns 0 on bad arguments. */
+size_t svlcov_workspace_bytes(const svlcov_init_desc* d);
+
+/* Create a handle from a starting rank-k SVD (Section 3.2: U' <- U, V' <- V,
+ * U'' = V'' = I).  Copies U0 / V0 into ubuf / vbuf (converted to the storage
+ * dtype) and sigma0 into the workspace, on `stream`.  *h receives a host
+ * object freed by svlcov_destroy.  The first call on a device also selects
+ * kernel attributes (no allocation). */
+int svlcov_init(svlcov_handle** h, const svlcov_init_desc* d, void* stream);
+
+/* Add columns: A <- [A  E_c] (Algorithm 3; Section 3.2 for the folds).
+ * Ec_T: CSR with s rows (the new columns) of length m.  U' receives a sparse
+ * addition on the rows the batch touches; s rows are appended to V'
+ * (n <- n + s).  Host errors: INVALID_ARG (cols != m, s > max_s), CAPACITY
+ * (n + s > max_n, nnz > max_nnz). */
+int svlcov_add_cols(svlcov_handle* h, const svlcov_csr* Ec_T, void* stream);
+
+/* Add rows: A <- [A ; E_r] (Algorithm 11).  Er: CSR with s rows of length n.
+ * V' receives the sparse addition, s rows are appended to U' (m <- m + s).
+ * Algorithm 11 is Algorithm 3 applied to A^T; the library runs the same
+ * kernels with the roles of U and V exchanged. */
+int svlcov_add_rows(svlcov_handle* h, const svlcov_csr* Er, void* stream);
+
+/* Update weights: A <- A + D E_m^T (Algorithm 4).  D_T: CSR s x m (columns of
+ * D), Em_T: CSR s x n (columns of E_m), same s.  U' and V' both receive
+ * sparse additions; no rows are appended. */
+int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T,
+                          void* stream);
+
+/* Materialise U = U' U'' (m x k), Sigma (k) and V = V' V'' (n x k) into
+ * caller buffers (device; row-major; out_dtype SVLCOV_FP64 or FP32; any of
+ * the three pointers may be NULL to skip it).  m and n are the current shape
+ * (svlcov_get_shape). */
+int svlcov_get_factors(svlcov_handle* h, void* U, double* sigma, void* V, int32_t out_dtype,
+                       void* stream);
+
+/* Query rows (Theorem 1, Query: U[i] = U'[i] U'' in O(k^2)).  side 0 = U,
+ * 1 = V; idx: device, cnt row indices (must be < current m or n; rows out of
+ * range are written as zeros and flag SVLCOV_DEV_BAD_CSR); out: device,
+ * cnt x k row-major of out_dtype. */
+int svlcov_query_rows(svlcov_handle* h, int32_t side, const int32_t* idx, int32_t cnt, void* out,
+                      int32_t out_dtype, void* stream);
+
+/* Current shape as the host sees it (m, n grow with every append). */
+int svlcov_get_shape(const svlcov_handle* h, int64_t* m, int64_t* n, int32_t* k);
+
+/* Synchronise `stream`, read and clear the device status word into
+ * *device_code (0 = no error).  After an error the host shape is restored
+ * from the device's committed counters. */
+int svlcov_status(svlcov_handle* h, int32_t* device_code, void* stream);
+
+/* Copy the small state (FP64, host buffers): Wu = U'' (k x k row-major),
+ * Wv = V'' and sigma; any pointer may be NULL.  Synchronises `stream`.
+ * Also returns the number of resets performed so far in *resets (may be
+ * NULL). */
+int svlcov_get_small_state(svlcov_handle* h, double* Wu, double* Wv, double* sigma,
+                           int64_t* resets, void* stream);
+
+/* Checkpoint support.  get_state copies U' (m x k), V' (n x k) in the storage
+ * dtype and U'', V'', Sigma (FP64) to host buffers; set_state loads them back
+ * (shape given by m, n; both synchronise `stream`).  Resuming from a state is
+ * bit-identical to never having stopped. */
+int svlcov_get_state(svlcov_handle* h, void* Up_host, void* Vp_host, double* Wu_host,
+                     double* Wv_host, double* sigma_host, void* stream);
+int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host,
+                     const void* Vp_host, const double* Wu_host, const double* Wv_host,
+                     const double* sigma_host, void* stream);
+
+/* Intermediates of the last step, for per-kernel checks (FP64 host copies,
+ * synchronises).  which: 0 = P = X'^T E (k x s), 1 = S_E = E^T E (s x s),
+ * 2 = C0 (k x s), 3 = R (s x s), 4 = K ((k+s) x (k+s)), 5 = Theta (k),
+ * 6 = F ((k+s) x k), 7 = G ((k+s) x k).  side selects D (0) or E (1) for a
+ * weight update.  Column-major; *rows, *cols receive the shape. */
+int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
+                            size_t capacity_doubles, int32_t* rows, int32_t* cols, void* stream);
+
+/* Release the host object (device buffers stay with the caller). */
+void svlcov_destroy(svlcov_handle* h);
+
+/* Human-readable name of a return or status code. */
+const char* svlcov_strerror(int32_t code);
+
+/* ---- standalone dense kernels (same code as inside a step) -------------- */
+
+/* Rank-k SVD of a small dense matrix (the Rayleigh-Ritz step of Section 2.1,
+ * SVD_k of K): one-sided Jacobi.  K: device, n x n column-major FP64 (not
+ * modified).  F (n x k), theta (k), G (n x k): device FP64 outputs,
+ * column-major, theta descending.  precision: SVLCOV_SMALL_*.  work: device
+ * scratch of svlcov_small_svd_work_bytes(n) bytes.  Returns the number of
+ * sweeps in *sweeps (host, may be NULL; synchronises when non-NULL). */
+size_t svlcov_small_svd_work_bytes(int32_t n);
+int svlcov_small_svd(const double* K, int32_t n, int32_t k, double* F, double* theta, double* G,
+                     int32_t precision, void* work, int32_t* sweeps, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* SVLCOV_H */

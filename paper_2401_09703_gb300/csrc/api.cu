@@ -1,0 +1,642 @@
+// C ABI of the SV-LCOV GB300 library: handle, workspace layout and the launch
+// sequence of one update step (Algorithms 3, 4 and 11 on the extended
+// decomposition of Section 3.2).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "kernels.cuh"
+
+using namespace svl;
+
+namespace {
+
+// ---- workspace carving ------------------------------------------------------
+struct Carver {
+  char* base;
+  size_t off = 0;
+  explicit Carver(void* b) : base((char*)b) {}
+  template <typename T> T* take(size_t count) {
+    off = (off + 255) & ~(size_t)255;
+    T* p = base ? (T*)(base + off) : nullptr;
+    off += count * sizeof(T);
+    return p;
+  }
+};
+
+struct SideBufs {
+  SideScratch sc;
+  double *P, *SE, *C0, *e2, *S, *L1, *Y1, *T1, *S2, *L2, *Y2, *R, *X, *CQ, *Lm, *Y, *Mt;
+  unsigned char *defl1, *defl2;
+};
+
+int log2_ceil(int64_t v) {
+  int l = 0;
+  while (((int64_t)1 << l) < v) ++l;
+  return l;
+}
+
+}  // namespace
+
+struct svlcov_handle {
+  svlcov_init_desc d;
+  int64_t m, n;  // host view of the shape
+  int k;
+  int64_t Hmax;
+  // persistent device state
+  int* status;
+  int64_t* counters;  // [0] m, [1] n committed
+  int64_t* resets;
+  int* flags;         // [0] reset_u, [1] reset_v
+  double *Wu, *Wv, *sigma;
+  // step scratch
+  SideBufs side[2];
+  double *K, *F, *G, *theta, *Xu, *Xv, *Wu_new, *Wv_new, *Wu_inv, *Wv_inv, *Nt;
+  void* jwork;
+  // bookkeeping of the last step
+  int last_op = -1, last_s = 0;
+};
+
+static void layout(svlcov_handle* h, void* base, size_t* total) {
+  const svlcov_init_desc& d = h->d;
+  int64_t k = d.k, s = d.max_s, n2 = k + s, nnz = std::max<int64_t>(d.max_nnz, 1);
+  int64_t H = h->Hmax, ch = max_chunks(s, nnz);
+  Carver c(base);
+  h->status = c.take<int>(4);
+  h->counters = c.take<int64_t>(4);
+  h->resets = c.take<int64_t>(2);
+  h->flags = c.take<int>(8);
+  h->Wu = c.take<double>(k * k);
+  h->Wv = c.take<double>(k * k);
+  h->sigma = c.take<double>(k);
+  for (int sd = 0; sd < 2; ++sd) {
+    SideBufs& b = h->side[sd];
+    b.sc.rowid = c.take<int>(nnz);
+    b.sc.slot = c.take<int>(nnz);
+    b.sc.rank_tmp = c.take<int>(nnz);
+    b.sc.tmp_j = c.take<int>(nnz);
+    b.sc.tmp_e = c.take<int>(nnz);
+    b.sc.seg_j = c.take<int>(nnz);
+    b.sc.seg_v = c.take<double>(nnz);
+    b.sc.hkey = c.take<int>(H);
+    b.sc.hcnt = c.take<int>(H);
+    b.sc.hstart = c.take<int>(H);
+    b.sc.occ = c.take<int>(H);
+    b.sc.counts = c.take<int>(4);
+    b.sc.chunk_off = c.take<int>(s + 1);
+    b.sc.chunk_row = c.take<int>(ch);
+    b.sc.Ppart = c.take<double>(ch * k);
+    b.sc.SEpart = c.take<double>(ch * s);
+    b.P = c.take<double>(k * s);
+    b.SE = c.take<double>(s * s);
+    b.C0 = c.take<double>(k * s);
+    b.e2 = c.take<double>(s);
+    b.S = c.take<double>(s * s);
+    b.L1 = c.take<double>(s * s);
+    b.Y1 = c.take<double>(s * s);
+    b.T1 = c.take<double>(s * s);
+    b.S2 = c.take<double>(s * s);
+    b.L2 = c.take<double>(s * s);
+    b.Y2 = c.take<double>(s * s);
+    b.R = c.take<double>(s * s);
+    b.X = c.take<double>(s * s);
+    b.CQ = c.take<double>(k * s);
+    b.Lm = c.take<double>(n2 * s);
+    b.Y = c.take<double>(s * k);
+    b.Mt = c.take<double>(k * s);
+    b.defl1 = c.take<unsigned char>(s);
+    b.defl2 = c.take<unsigned char>(s);
+  }
+  h->K = c.take<double>(n2 * n2);
+  h->F = c.take<double>(n2 * k);
+  h->G = c.take<double>(n2 * k);
+  h->theta = c.take<double>(k);
+  h->Xu = c.take<double>(k * k);
+  h->Xv = c.take<double>(k * k);
+  h->Wu_new = c.take<double>(k * k);
+  h->Wv_new = c.take<double>(k * k);
+  h->Wu_inv = c.take<double>(k * k);
+  h->Wv_inv = c.take<double>(k * k);
+  h->Nt = c.take<double>(k * s);
+  h->jwork = c.take<char>(jacobi_work_bytes((int)n2));
+  *total = (c.off + 255) & ~(size_t)255;
+}
+
+static bool desc_ok(const svlcov_init_desc* d) {
+  if (!d) return false;
+  if (d->k < 1 || d->k > SVLCOV_MAX_K) return false;
+  if (d->max_s < 1 || d->max_s > SVLCOV_MAX_S) return false;
+  if (d->m < 0 || d->n < 0 || d->max_m < d->m || d->max_n < d->n || d->max_nnz < 0) return false;
+  if (d->storage < SVLCOV_FP64 || d->storage > SVLCOV_BF16) return false;
+  if (d->small < SVLCOV_SMALL_FP64 || d->small > SVLCOV_SMALL_MIXED) return false;
+  return true;
+}
+
+static bool small_is_f32(const svlcov_handle* h) { return h->d.small == SVLCOV_SMALL_FP32; }
+
+extern "C" size_t svlcov_workspace_bytes(const svlcov_init_desc* d) {
+  if (!desc_ok(d)) return 0;
+  svlcov_handle tmp;
+  tmp.d = *d;
+  tmp.k = d->k;
+  tmp.Hmax = (int64_t)1 << std::max(4, log2_ceil(2 * std::max<int64_t>(d->max_nnz, 1)));
+  size_t total = 0;
+  layout(&tmp, nullptr, &total);
+  return total;
+}
+
+#define CUDA_OK(x)                                    \
+  do {                                                \
+    cudaError_t e_ = (x);                             \
+    if (e_ != cudaSuccess) return SVLCOV_ERR_CUDA;    \
+  } while (0)
+
+static int last_launch() { return cudaGetLastError() == cudaSuccess ? SVLCOV_OK : SVLCOV_ERR_CUDA; }
+
+template <typename TC>
+static void init_small(svlcov_handle* h, cudaStream_t st) {
+  launch_set_identity<TC>((TC*)h->Wu, h->k, st);
+  launch_set_identity<TC>((TC*)h->Wv, h->k, st);
+  if (sizeof(TC) == 8) cudaMemcpyAsync(h->sigma, h->d.sigma0, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, st);
+  else launch_cast<double, float>(h->d.sigma0, (float*)h->sigma, h->k, st);
+}
+
+template <typename TS>
+static void init_factors(svlcov_handle* h, cudaStream_t st) {
+  launch_convert_in<TS>(h->d.U0, h->d.init_dtype, (TS*)h->d.ubuf, h->d.m * h->d.k, st);
+  launch_convert_in<TS>(h->d.V0, h->d.init_dtype, (TS*)h->d.vbuf, h->d.n * h->d.k, st);
+}
+
+extern "C" int svlcov_init(svlcov_handle** out, const svlcov_init_desc* d, void* stream) {
+  if (!out || !desc_ok(d)) return SVLCOV_ERR_INVALID_ARG;
+  if (!d->ubuf || !d->vbuf || !d->workspace || !d->sigma0) return SVLCOV_ERR_INVALID_ARG;
+  if ((d->m > 0 && !d->U0) || (d->n > 0 && !d->V0)) return SVLCOV_ERR_INVALID_ARG;
+  if (d->init_dtype != SVLCOV_FP64 && d->init_dtype != SVLCOV_FP32) return SVLCOV_ERR_INVALID_ARG;
+  if (((uintptr_t)d->workspace & 255) != 0) return SVLCOV_ERR_INVALID_ARG;
+  size_t need = svlcov_workspace_bytes(d);
+  if (need == 0 || d->workspace_bytes < need) return SVLCOV_ERR_CAPACITY;
+  svlcov_handle* h = new (std::nothrow) svlcov_handle();
+  if (!h) return SVLCOV_ERR_INVALID_ARG;
+  h->d = *d;
+  h->k = d->k;
+  h->m = d->m;
+  h->n = d->n;
+  h->Hmax = (int64_t)1 << std::max(4, log2_ceil(2 * std::max<int64_t>(d->max_nnz, 1)));
+  if (h->d.tau <= 0) h->d.tau = d->small == SVLCOV_SMALL_FP32 ? 1e-6 : 1e-12;
+  if (h->d.reset_threshold <= 0)
+    h->d.reset_threshold = d->storage == SVLCOV_FP64 ? 1e8 : (d->storage == SVLCOV_FP32 ? 1e2 : 1e1);
+  size_t total = 0;
+  layout(h, d->workspace, &total);
+  cudaStream_t st = (cudaStream_t)stream;
+  cudaMemsetAsync(h->status, 0, sizeof(int) * 4, st);
+  cudaMemsetAsync(h->resets, 0, sizeof(int64_t) * 2, st);
+  cudaMemsetAsync(h->flags, 0, sizeof(int) * 8, st);
+  int64_t counters[4] = {d->m, d->n, 0, 0};
+  cudaMemcpyAsync(h->counters, counters, sizeof(counters), cudaMemcpyHostToDevice, st);
+  cudaStreamSynchronize(st);  // the host array above must outlive the copy
+  if (small_is_f32(h)) init_small<float>(h, st);
+  else init_small<double>(h, st);
+  if (d->storage == SVLCOV_FP64) init_factors<double>(h, st);
+  else if (d->storage == SVLCOV_FP32) init_factors<float>(h, st);
+  else init_factors<__nv_bfloat16>(h, st);
+  if (last_launch() != SVLCOV_OK) {
+    delete h;
+    return SVLCOV_ERR_CUDA;
+  }
+  *out = h;
+  return SVLCOV_OK;
+}
+
+extern "C" void svlcov_destroy(svlcov_handle* h) { delete h; }
+
+// ---------------------------------------------------------------------------
+// One side of Algorithm 2 in the CholeskyQR2 form: from the batch, the
+// projected factor X' and its small factor W, compute C0 = W^T X'^T E, the
+// residual Gram S = E^T E - C0^T C0, R = R2 R1 and X = R^-1 (with dropped
+// directions zeroed), and C_Q = C0 X (so that B = E X and Q = B - U C_Q).
+template <typename TS, typename TC>
+static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, const TS* Xp, const TC* W, SideBufs& sb,
+                          cudaStream_t st) {
+  int k = h->k, s = b.rows;
+  int* status = h->status;
+  launch_validate(b, d_len, sb.sc.rowid, status, st);
+  int logH = std::max(4, log2_ceil(2 * std::max<int64_t>(b.nnz, 1)));
+  launch_group(b, logH, sb.sc, status, st);
+  TC *P = (TC*)sb.P, *SE = (TC*)sb.SE, *C0 = (TC*)sb.C0, *e2 = (TC*)sb.e2;
+  launch_gather_gram<TS, TC>(b, Xp, k, W, sb.sc, P, SE, C0, e2, status, st);
+  TC *S = (TC*)sb.S, *L1 = (TC*)sb.L1, *Y1 = (TC*)sb.Y1, *T1 = (TC*)sb.T1, *S2 = (TC*)sb.S2;
+  TC *L2 = (TC*)sb.L2, *Y2 = (TC*)sb.Y2, *R = (TC*)sb.R, *X = (TC*)sb.X, *CQ = (TC*)sb.CQ;
+  launch_copy<TC>(SE, S, (int64_t)s * s, status, st);
+  gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);        // S = S_E - C0^T C0
+  TC tau = (TC)h->d.tau;
+  launch_chol<TC>(S, s, e2, tau, L1, sb.defl1, status, st);                              // S = L1 L1^T
+  launch_tri_inv<TC>(L1, s, sb.defl1, Y1, status, st);                                   // Y1 = L1^-1
+  gemm<TC>(false, true, s, s, s, (TC)1, S, s, Y1, s, (TC)0, T1, s, status, st);         // T1 = S Y1^T
+  gemm<TC>(false, false, s, s, s, (TC)1, Y1, s, T1, s, (TC)0, S2, s, status, st);       // S2 = Y1 S Y1^T
+  launch_chol<TC>(S2, s, nullptr, tau, L2, sb.defl2, status, st);                        // S2 = L2 L2^T
+  launch_tri_inv<TC>(L2, s, sb.defl2, Y2, status, st);
+  gemm<TC>(true, true, s, s, s, (TC)1, L2, s, L1, s, (TC)0, R, s, status, st);           // R = L2^T L1^T
+  gemm<TC>(true, true, s, s, s, (TC)1, Y1, s, Y2, s, (TC)0, X, s, status, st);           // X = Y1^T Y2^T
+  gemm<TC>(false, false, k, s, s, (TC)1, C0, k, X, s, (TC)0, CQ, k, status, st);         // C_Q = C0 X
+}
+
+// Fold of one projected side (Section 3.2): Xn = W (Fk - C_Q Fs), Winv, and
+// Mt = (X Fs Xn^-1)^T, the rows added to X' at the batch's touched rows.
+template <typename TC>
+static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC* Fbig, int n2, int s, TC* Xtmp,
+                           TC* Wn, TC* Winv, int* reset_flag, cudaStream_t st) {
+  int k = h->k;
+  int* status = h->status;
+  launch_copy2d<TC>(Fbig, n2, Xtmp, k, k, k, status, st);                                             // Fk
+  gemm<TC>(false, false, k, k, s, (TC)-1, (TC*)sb.CQ, k, Fbig + k, n2, (TC)1, Xtmp, k, status, st);  // - C_Q Fs
+  gemm<TC>(false, false, k, k, k, (TC)1, W, k, Xtmp, k, (TC)0, Wn, k, status, st);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st);
+  gemm<TC>(false, false, s, k, s, (TC)1, (TC*)sb.X, s, Fbig + k, n2, (TC)0, (TC*)sb.Y, s, status, st);
+  gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
+}
+
+template <typename TS, typename TC>
+static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream_t st) {
+  int k = h->k, s = b.rows, n2 = k + s;
+  int* status = h->status;
+  SideBufs& sb = h->side[0];
+  // projected side P and appended side O
+  TS* XpP = (TS*)(cols ? h->d.ubuf : h->d.vbuf);
+  TS* XpO = (TS*)(cols ? h->d.vbuf : h->d.ubuf);
+  TC* WP = (TC*)(cols ? h->Wu : h->Wv);
+  TC* WO = (TC*)(cols ? h->Wv : h->Wu);
+  TC* WPn = (TC*)(cols ? h->Wu_new : h->Wv_new);
+  TC* WOn = (TC*)(cols ? h->Wv_new : h->Wu_new);
+  TC* WPi = (TC*)(cols ? h->Wu_inv : h->Wv_inv);
+  TC* WOi = (TC*)(cols ? h->Wv_inv : h->Wu_inv);
+  int* rP = h->flags + (cols ? 0 : 1);
+  int* rO = h->flags + (cols ? 1 : 0);
+  int64_t rowsP = cols ? h->m : h->n, rowsO = cols ? h->n : h->m;
+  orthogonalise<TS, TC>(h, b, rowsP, XpP, WP, sb, st);
+  TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
+  launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
+  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st);               // F, Theta, G = SVD_k(K)
+  if (e) return SVLCOV_ERR_CUDA;
+  fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, st);
+  gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, st);      // W_O G[:k]
+  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st);
+  gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, n2, (TC)0, (TC*)h->Nt, k, status, st);  // (G[k:] W_O^-1)^T
+  FiniteSet<TC> fs{};
+  fs.ptr[0] = theta; fs.count[0] = k;
+  fs.ptr[1] = (TC*)sb.Mt; fs.count[1] = (int64_t)k * s;
+  fs.ptr[2] = (TC*)h->Nt; fs.count[2] = (int64_t)k * s;
+  fs.ptr[3] = WPn; fs.count[3] = (int64_t)k * k;
+  fs.ptr[4] = WOn; fs.count[4] = (int64_t)k * k;
+  fs.n = 5;
+  launch_check_finite_multi<TC>(fs, status, st);
+  launch_reset<TS, TC>(XpP, rowsP, k, WPn, rP, status, st);   // only when the guard fired
+  launch_scatter<TS, TC>(XpP, k, (TC*)sb.Mt, b.nnz, sb.sc, status, st);
+  launch_reset<TS, TC>(XpO, rowsO, k, WOn, rO, status, st);
+  launch_append<TS, TC>(XpO, rowsO, k, s, (TC*)h->Nt, status, st);
+  if (cols)
+    launch_commit<TC>((TC*)h->Wu, WPn, rP, (TC*)h->Wv, WOn, rO, (TC*)h->sigma, theta, k, h->counters, 0, s,
+                      h->resets, status, st);
+  else
+    launch_commit<TC>((TC*)h->Wu, WOn, rO, (TC*)h->Wv, WPn, rP, (TC*)h->sigma, theta, k, h->counters, s, 0,
+                      h->resets, status, st);
+  return last_launch();
+}
+
+template <typename TS, typename TC>
+static int step_weights(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr& E, cudaStream_t st) {
+  int k = h->k, s = D.rows, n2 = k + s;
+  int* status = h->status;
+  SideBufs& sd = h->side[0];
+  SideBufs& se = h->side[1];
+  orthogonalise<TS, TC>(h, D, h->m, (TS*)h->d.ubuf, (TC*)h->Wu, sd, st);
+  orthogonalise<TS, TC>(h, E, h->n, (TS*)h->d.vbuf, (TC*)h->Wv, se, st);
+  TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
+  launch_build_L<TC>((TC*)sd.C0, (TC*)sd.R, k, s, (TC*)sd.Lm, status, st);
+  launch_build_L<TC>((TC*)se.C0, (TC*)se.R, k, s, (TC*)se.Lm, status, st);
+  gemm<TC>(false, true, n2, n2, s, (TC)1, (TC*)sd.Lm, n2, (TC*)se.Lm, n2, (TC)0, K, n2, status, st);
+  launch_add_diag<TC>(K, n2, (TC*)h->sigma, k, status, st);   // K = diag(S,0) + [C0D;RD][C0E;RE]^T
+  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st);
+  if (e) return SVLCOV_ERR_CUDA;
+  fold_projected<TC>(h, sd, (TC*)h->Wu, F, n2, s, (TC*)h->Xu, (TC*)h->Wu_new, (TC*)h->Wu_inv, h->flags + 0, st);
+  fold_projected<TC>(h, se, (TC*)h->Wv, G, n2, s, (TC*)h->Xv, (TC*)h->Wv_new, (TC*)h->Wv_inv, h->flags + 1, st);
+  FiniteSet<TC> fs{};
+  fs.ptr[0] = theta; fs.count[0] = k;
+  fs.ptr[1] = (TC*)sd.Mt; fs.count[1] = (int64_t)k * s;
+  fs.ptr[2] = (TC*)se.Mt; fs.count[2] = (int64_t)k * s;
+  fs.ptr[3] = (TC*)h->Wu_new; fs.count[3] = (int64_t)k * k;
+  fs.ptr[4] = (TC*)h->Wv_new; fs.count[4] = (int64_t)k * k;
+  fs.n = 5;
+  launch_check_finite_multi<TC>(fs, status, st);
+  launch_reset<TS, TC>((TS*)h->d.ubuf, h->m, k, (TC*)h->Wu_new, h->flags + 0, status, st);
+  launch_scatter<TS, TC>((TS*)h->d.ubuf, k, (TC*)sd.Mt, D.nnz, sd.sc, status, st);
+  launch_reset<TS, TC>((TS*)h->d.vbuf, h->n, k, (TC*)h->Wv_new, h->flags + 1, status, st);
+  launch_scatter<TS, TC>((TS*)h->d.vbuf, k, (TC*)se.Mt, E.nnz, se.sc, status, st);
+  launch_commit<TC>((TC*)h->Wu, (TC*)h->Wu_new, h->flags + 0, (TC*)h->Wv, (TC*)h->Wv_new, h->flags + 1,
+                    (TC*)h->sigma, theta, k, h->counters, 0, 0, h->resets, status, st);
+  return last_launch();
+}
+
+template <typename TC>
+static int dispatch_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream_t st) {
+  switch (h->d.storage) {
+    case SVLCOV_FP64: return step_add<double, TC>(h, b, cols, st);
+    case SVLCOV_FP32: return step_add<float, TC>(h, b, cols, st);
+    default: return step_add<__nv_bfloat16, TC>(h, b, cols, st);
+  }
+}
+
+template <typename TC>
+static int dispatch_weights(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr& E, cudaStream_t st) {
+  switch (h->d.storage) {
+    case SVLCOV_FP64: return step_weights<double, TC>(h, D, E, st);
+    case SVLCOV_FP32: return step_weights<float, TC>(h, D, E, st);
+    default: return step_weights<__nv_bfloat16, TC>(h, D, E, st);
+  }
+}
+
+static bool csr_ok(const svlcov_csr* b) {
+  if (!b) return false;
+  if (b->rows < 0 || b->cols < 0 || b->nnz < 0) return false;
+  if (b->values_dtype != SVLCOV_FP64 && b->values_dtype != SVLCOV_FP32) return false;
+  if (b->rows > 0 && !b->indptr) return false;
+  if (b->nnz > 0 && (!b->indices || !b->values)) return false;
+  return true;
+}
+
+static int do_add(svlcov_handle* h, const svlcov_csr* b, bool cols, void* stream) {
+  if (!h || !csr_ok(b)) return SVLCOV_ERR_INVALID_ARG;
+  int64_t d_len = cols ? h->m : h->n;
+  if (b->cols != d_len) return SVLCOV_ERR_INVALID_ARG;
+  if (b->rows > h->d.max_s || b->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
+  if (cols ? (h->n + b->rows > h->d.max_n) : (h->m + b->rows > h->d.max_m)) return SVLCOV_ERR_CAPACITY;
+  if (b->rows == 0) return SVLCOV_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = small_is_f32(h) ? dispatch_add<float>(h, *b, cols, st) : dispatch_add<double>(h, *b, cols, st);
+  if (rc == SVLCOV_OK) {
+    if (cols) h->n += b->rows;
+    else h->m += b->rows;
+    h->last_op = cols ? 0 : 1;
+    h->last_s = b->rows;
+  }
+  return rc;
+}
+
+extern "C" int svlcov_add_cols(svlcov_handle* h, const svlcov_csr* Ec_T, void* stream) {
+  return do_add(h, Ec_T, true, stream);
+}
+
+extern "C" int svlcov_add_rows(svlcov_handle* h, const svlcov_csr* Er, void* stream) {
+  return do_add(h, Er, false, stream);
+}
+
+extern "C" int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T, void* stream) {
+  if (!h || !csr_ok(D_T) || !csr_ok(Em_T)) return SVLCOV_ERR_INVALID_ARG;
+  if (D_T->cols != h->m || Em_T->cols != h->n || D_T->rows != Em_T->rows) return SVLCOV_ERR_INVALID_ARG;
+  if (D_T->rows > h->d.max_s || D_T->nnz > h->d.max_nnz || Em_T->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
+  if (D_T->rows == 0) return SVLCOV_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = small_is_f32(h) ? dispatch_weights<float>(h, *D_T, *Em_T, st)
+                           : dispatch_weights<double>(h, *D_T, *Em_T, st);
+  if (rc == SVLCOV_OK) {
+    h->last_op = 2;
+    h->last_s = D_T->rows;
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+template <typename TS, typename TC>
+static void materialize_side(svlcov_handle* h, int side, void* out, int out_dtype, const int32_t* idx, int64_t cnt,
+                             cudaStream_t st) {
+  const TS* Xp = (const TS*)(side == 0 ? h->d.ubuf : h->d.vbuf);
+  const TC* W = (const TC*)(side == 0 ? h->Wu : h->Wv);
+  int64_t rows = side == 0 ? h->m : h->n;
+  launch_materialize<TS, TC>(Xp, idx ? cnt : rows, rows, h->k, W, out, out_dtype, idx, st, h->status);
+}
+
+template <typename TC>
+static void materialize_dispatch(svlcov_handle* h, int side, void* out, int out_dtype, const int32_t* idx,
+                                 int64_t cnt, cudaStream_t st) {
+  switch (h->d.storage) {
+    case SVLCOV_FP64: materialize_side<double, TC>(h, side, out, out_dtype, idx, cnt, st); break;
+    case SVLCOV_FP32: materialize_side<float, TC>(h, side, out, out_dtype, idx, cnt, st); break;
+    default: materialize_side<__nv_bfloat16, TC>(h, side, out, out_dtype, idx, cnt, st); break;
+  }
+}
+
+extern "C" int svlcov_get_factors(svlcov_handle* h, void* U, double* sigma, void* V, int32_t out_dtype,
+                                  void* stream) {
+  if (!h || (out_dtype != SVLCOV_FP64 && out_dtype != SVLCOV_FP32)) return SVLCOV_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  bool f32 = small_is_f32(h);
+  if (U) f32 ? materialize_dispatch<float>(h, 0, U, out_dtype, nullptr, 0, st)
+             : materialize_dispatch<double>(h, 0, U, out_dtype, nullptr, 0, st);
+  if (V) f32 ? materialize_dispatch<float>(h, 1, V, out_dtype, nullptr, 0, st)
+             : materialize_dispatch<double>(h, 1, V, out_dtype, nullptr, 0, st);
+  if (sigma) {
+    if (f32) launch_cast<float, double>((const float*)h->sigma, sigma, h->k, st);
+    else cudaMemcpyAsync(sigma, h->sigma, sizeof(double) * h->k, cudaMemcpyDeviceToDevice, st);
+  }
+  return last_launch();
+}
+
+extern "C" int svlcov_query_rows(svlcov_handle* h, int32_t side, const int32_t* idx, int32_t cnt, void* out,
+                                 int32_t out_dtype, void* stream) {
+  if (!h || (side != 0 && side != 1) || cnt < 0 || (cnt > 0 && (!idx || !out))) return SVLCOV_ERR_INVALID_ARG;
+  if (out_dtype != SVLCOV_FP64 && out_dtype != SVLCOV_FP32) return SVLCOV_ERR_INVALID_ARG;
+  if (cnt == 0) return SVLCOV_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (small_is_f32(h)) materialize_dispatch<float>(h, side, out, out_dtype, idx, cnt, st);
+  else materialize_dispatch<double>(h, side, out, out_dtype, idx, cnt, st);
+  return last_launch();
+}
+
+extern "C" int svlcov_get_shape(const svlcov_handle* h, int64_t* m, int64_t* n, int32_t* k) {
+  if (!h) return SVLCOV_ERR_INVALID_ARG;
+  if (m) *m = h->m;
+  if (n) *n = h->n;
+  if (k) *k = h->k;
+  return SVLCOV_OK;
+}
+
+extern "C" int svlcov_status(svlcov_handle* h, int32_t* device_code, void* stream) {
+  if (!h) return SVLCOV_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_OK(cudaStreamSynchronize(st));
+  int code = 0;
+  CUDA_OK(cudaMemcpy(&code, h->status, sizeof(int), cudaMemcpyDeviceToHost));
+  if (code != 0) {
+    int64_t c[2];
+    CUDA_OK(cudaMemcpy(c, h->counters, sizeof(c), cudaMemcpyDeviceToHost));
+    h->m = c[0];
+    h->n = c[1];
+    CUDA_OK(cudaMemset(h->status, 0, sizeof(int)));
+  }
+  if (device_code) *device_code = code;
+  return SVLCOV_OK;
+}
+
+static int copy_small_to_host(svlcov_handle* h, const double* src, double* dst, int64_t count) {
+  if (!dst) return SVLCOV_OK;
+  if (small_is_f32(h)) {
+    std::vector<float> tmp(count);
+    CUDA_OK(cudaMemcpy(tmp.data(), src, sizeof(float) * count, cudaMemcpyDeviceToHost));
+    for (int64_t i = 0; i < count; ++i) dst[i] = tmp[i];
+  } else {
+    CUDA_OK(cudaMemcpy(dst, src, sizeof(double) * count, cudaMemcpyDeviceToHost));
+  }
+  return SVLCOV_OK;
+}
+
+static int copy_small_from_host(svlcov_handle* h, const double* src, double* dst, int64_t count) {
+  if (!src) return SVLCOV_OK;
+  if (small_is_f32(h)) {
+    std::vector<float> tmp(count);
+    for (int64_t i = 0; i < count; ++i) tmp[i] = (float)src[i];
+    CUDA_OK(cudaMemcpy(dst, tmp.data(), sizeof(float) * count, cudaMemcpyHostToDevice));
+  } else {
+    CUDA_OK(cudaMemcpy(dst, src, sizeof(double) * count, cudaMemcpyHostToDevice));
+  }
+  return SVLCOV_OK;
+}
+
+// k x k small matrices are column-major on the device; the host API is row-major.
+static void transpose_sq(double* a, int k) {
+  for (int i = 0; i < k; ++i)
+    for (int j = i + 1; j < k; ++j) std::swap(a[i * k + j], a[j * k + i]);
+}
+
+extern "C" int svlcov_get_small_state(svlcov_handle* h, double* Wu, double* Wv, double* sigma, int64_t* resets,
+                                      void* stream) {
+  if (!h) return SVLCOV_ERR_INVALID_ARG;
+  CUDA_OK(cudaStreamSynchronize((cudaStream_t)stream));
+  int k = h->k;
+  int rc;
+  if ((rc = copy_small_to_host(h, h->Wu, Wu, (int64_t)k * k))) return rc;
+  if ((rc = copy_small_to_host(h, h->Wv, Wv, (int64_t)k * k))) return rc;
+  if ((rc = copy_small_to_host(h, h->sigma, sigma, k))) return rc;
+  if (Wu) transpose_sq(Wu, k);
+  if (Wv) transpose_sq(Wv, k);
+  if (resets) CUDA_OK(cudaMemcpy(resets, h->resets, sizeof(int64_t), cudaMemcpyDeviceToHost));
+  return SVLCOV_OK;
+}
+
+static size_t storage_elem(const svlcov_handle* h) {
+  return h->d.storage == SVLCOV_FP64 ? 8 : (h->d.storage == SVLCOV_FP32 ? 4 : 2);
+}
+
+extern "C" int svlcov_get_state(svlcov_handle* h, void* Up_host, void* Vp_host, double* Wu_host, double* Wv_host,
+                                double* sigma_host, void* stream) {
+  if (!h) return SVLCOV_ERR_INVALID_ARG;
+  CUDA_OK(cudaStreamSynchronize((cudaStream_t)stream));
+  size_t es = storage_elem(h);
+  if (Up_host) CUDA_OK(cudaMemcpy(Up_host, h->d.ubuf, es * h->m * h->k, cudaMemcpyDeviceToHost));
+  if (Vp_host) CUDA_OK(cudaMemcpy(Vp_host, h->d.vbuf, es * h->n * h->k, cudaMemcpyDeviceToHost));
+  return svlcov_get_small_state(h, Wu_host, Wv_host, sigma_host, nullptr, stream);
+}
+
+extern "C" int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host, const void* Vp_host,
+                                const double* Wu_host, const double* Wv_host, const double* sigma_host,
+                                void* stream) {
+  if (!h || m < 0 || n < 0 || m > h->d.max_m || n > h->d.max_n) return SVLCOV_ERR_INVALID_ARG;
+  if (!Up_host || !Vp_host || !Wu_host || !Wv_host || !sigma_host) return SVLCOV_ERR_INVALID_ARG;
+  CUDA_OK(cudaStreamSynchronize((cudaStream_t)stream));
+  size_t es = storage_elem(h);
+  int k = h->k;
+  CUDA_OK(cudaMemcpy(h->d.ubuf, Up_host, es * m * k, cudaMemcpyHostToDevice));
+  CUDA_OK(cudaMemcpy(h->d.vbuf, Vp_host, es * n * k, cudaMemcpyHostToDevice));
+  std::vector<double> wu(Wu_host, Wu_host + (size_t)k * k), wv(Wv_host, Wv_host + (size_t)k * k);
+  transpose_sq(wu.data(), k);
+  transpose_sq(wv.data(), k);
+  int rc;
+  if ((rc = copy_small_from_host(h, wu.data(), h->Wu, (int64_t)k * k))) return rc;
+  if ((rc = copy_small_from_host(h, wv.data(), h->Wv, (int64_t)k * k))) return rc;
+  if ((rc = copy_small_from_host(h, sigma_host, h->sigma, k))) return rc;
+  int64_t c[4] = {m, n, 0, 0};
+  CUDA_OK(cudaMemcpy(h->counters, c, sizeof(c), cudaMemcpyHostToDevice));
+  CUDA_OK(cudaMemset(h->status, 0, sizeof(int)));
+  h->m = m;
+  h->n = n;
+  return SVLCOV_OK;
+}
+
+extern "C" int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
+                                       size_t capacity, int32_t* rows, int32_t* cols, void* stream) {
+  if (!h || side < 0 || side > 1 || h->last_op < 0) return SVLCOV_ERR_INVALID_ARG;
+  int k = h->k, s = h->last_s, n2 = k + s;
+  const SideBufs& sb = h->side[side];
+  const double* src = nullptr;
+  int r = 0, c = 0;
+  switch (which) {
+    case 0: src = sb.P; r = k; c = s; break;
+    case 1: src = sb.SE; r = s; c = s; break;
+    case 2: src = sb.C0; r = k; c = s; break;
+    case 3: src = sb.R; r = s; c = s; break;
+    case 4: src = h->K; r = n2; c = n2; break;
+    case 5: src = h->theta; r = k; c = 1; break;
+    case 6: src = h->F; r = n2; c = k; break;
+    case 7: src = h->G; r = n2; c = k; break;
+    default: return SVLCOV_ERR_INVALID_ARG;
+  }
+  if (rows) *rows = r;
+  if (cols) *cols = c;
+  if (!host_out) return SVLCOV_OK;
+  if ((size_t)r * c > capacity) return SVLCOV_ERR_CAPACITY;
+  CUDA_OK(cudaStreamSynchronize((cudaStream_t)stream));
+  return copy_small_to_host(h, src, host_out, (int64_t)r * c);
+}
+
+extern "C" const char* svlcov_strerror(int32_t code) {
+  switch (code) {
+    case SVLCOV_OK: return "ok";
+    case SVLCOV_ERR_INVALID_ARG: return "invalid argument";
+    case SVLCOV_ERR_CAPACITY: return "capacity exceeded";
+    case SVLCOV_ERR_CUDA: return "CUDA runtime error";
+    case SVLCOV_ERR_STATE: return "device error pending";
+    case SVLCOV_DEV_BAD_CSR: return "malformed CSR batch";
+    case SVLCOV_DEV_NONFINITE: return "non-finite value";
+    case SVLCOV_DEV_NOT_PD: return "residual Gram matrix not finite";
+    case SVLCOV_DEV_GAP_WARN: return "singular-value gap guard";
+    case SVLCOV_DEV_TIMEOUT: return "bounded device wait expired";
+    default: return "combination of device status bits";
+  }
+}
+
+// ---- standalone small SVD ----------------------------------------------------
+extern "C" size_t svlcov_small_svd_work_bytes(int32_t n) {
+  if (n <= 0) return 0;
+  return jacobi_work_bytes(n) + 3 * (size_t)n * n * sizeof(double) + 2 * n * sizeof(double) + 4096;
+}
+
+extern "C" int svlcov_small_svd(const double* K, int32_t n, int32_t k, double* F, double* theta, double* G,
+                                int32_t precision, void* work, int32_t* sweeps, void* stream) {
+  if (!K || !F || !theta || !G || !work || n <= 0 || k <= 0 || k > n) return SVLCOV_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  Carver c(work);
+  int* status = c.take<int>(4);
+  char* jw = c.take<char>(jacobi_work_bytes(n));
+  cudaMemsetAsync(status, 0, sizeof(int) * 4, st);
+  int e = 0;
+  if (precision == SVLCOV_SMALL_FP32) {
+    float* Kf = c.take<float>((size_t)n * n);
+    float* Ff = c.take<float>((size_t)n * k);
+    float* Gf = c.take<float>((size_t)n * k);
+    float* tf = c.take<float>(k);
+    launch_cast<double, float>(K, Kf, (int64_t)n * n, st);
+    e = launch_jacobi<float>(Kf, n, k, Ff, tf, Gf, jw, status, st);
+    launch_cast<float, double>(Ff, F, (int64_t)n * k, st);
+    launch_cast<float, double>(Gf, G, (int64_t)n * k, st);
+    launch_cast<float, double>(tf, theta, k, st);
+  } else {
+    e = launch_jacobi<double>(K, n, k, F, theta, G, jw, status, st);
+  }
+  if (e) return SVLCOV_ERR_CUDA;
+  if (sweeps) {
+    CUDA_OK(cudaStreamSynchronize(st));
+    int* sw = jacobi_sweeps_ptr(jw, n, precision == SVLCOV_SMALL_FP32 ? 4 : 8);
+    CUDA_OK(cudaMemcpy(sweeps, sw, sizeof(int), cudaMemcpyDeviceToHost));
+  }
+  return last_launch();
+}

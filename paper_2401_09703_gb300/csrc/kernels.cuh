@@ -1,0 +1,99 @@
+// Kernel launchers of the SV-LCOV GB300 library (host-side declarations).
+#pragma once
+#include "common.cuh"
+
+namespace svl {
+
+constexpr int kChunk = 32;  // nonzeros per gather/Gram work item (one warp)
+
+// Per-side scratch for one batch: CSR validation output, the hash-grouped
+// column view (entries grouped by their index into U'/V'), and the chunked
+// partial sums of the fused gather + Gram kernel.
+struct SideScratch {
+  int* rowid;      // [max_nnz]  batch row of each nonzero
+  int* slot;       // [max_nnz]  hash slot of each nonzero
+  int* rank_tmp;   // [max_nnz]
+  int* tmp_j;      // [max_nnz]
+  int* tmp_e;      // [max_nnz]
+  int* seg_j;      // [max_nnz]  grouped view: batch row, sorted within a group
+  double* seg_v;   // [max_nnz]  grouped view: value
+  int* hkey;       // [Hmax]
+  int* hcnt;       // [Hmax]
+  int* hstart;     // [Hmax]
+  int* occ;        // [Hmax]     occupied slots (distinct touched rows), count in counts[0]
+  int* counts;     // [4]        0: occupied slots, 1: total chunks
+  int* chunk_off;  // [max_s+1]
+  int* chunk_row;  // [max_chunks]
+  void* Ppart;     // [max_chunks * k] accumulator type
+  double* SEpart;  // [max_chunks * max_s]
+};
+
+int64_t max_chunks(int64_t max_s, int64_t max_nnz);
+
+// ---- sparse side (templated on storage TS and small-step type TC) ----------
+void launch_validate(const svlcov_csr& b, int64_t d, int* rowid, int* status, cudaStream_t st);
+void launch_group(const svlcov_csr& b, int logH, const SideScratch& w, int* status, cudaStream_t st);
+template <typename TS, typename TC>
+void launch_gather_gram(const svlcov_csr& b, const TS* Xp, int k, const TC* W, const SideScratch& w,
+                        TC* P, TC* SE, TC* C0, TC* e2, int* status, cudaStream_t st);
+template <typename TS, typename TC>
+void launch_scatter(TS* Xp, int k, const TC* Mt, int64_t nnz, const SideScratch& w, const int* status,
+                    cudaStream_t st);
+template <typename TS, typename TC>
+void launch_append(TS* Xp, int64_t row0, int k, int s, const TC* Nt, const int* status, cudaStream_t st);
+template <typename TS, typename TC>
+void launch_reset(TS* Xp, int64_t rows, int k, const TC* Wn, const int* do_reset, const int* status,
+                  cudaStream_t st);
+template <typename TS, typename TC>
+void launch_materialize(const TS* Xp, int64_t rows, int64_t src_rows, int k, const TC* W, void* out,
+                        int out_dtype, const int32_t* idx, cudaStream_t st, int* status);
+template <typename TS>
+void launch_convert_in(const void* src, int src_dtype, TS* dst, int64_t count, cudaStream_t st);
+
+// ---- dense small steps (templated on TC) -----------------------------------
+template <typename T>
+void gemm(bool ta, bool tb, int M, int N, int Kd, T alpha, const T* A, int lda, const T* B, int ldb,
+          T beta, T* C, int ldc, const int* status, cudaStream_t st);
+template <typename T>
+void launch_syrk_sub(int s, int k, const T* C0, const T* SE, T* S, const int* status, cudaStream_t st);
+template <typename T>
+void launch_chol(const T* S, int s, const T* ref, T tau, T* L, unsigned char* defl, int* status,
+                 cudaStream_t st);
+template <typename T>
+void launch_tri_inv(const T* L, int s, const unsigned char* defl, T* Y, const int* status, cudaStream_t st);
+template <typename T>
+void launch_build_K_add(const T* sigma, const T* C0, const T* R, int k, int s, T* K, const int* status,
+                        cudaStream_t st);
+template <typename T>
+void launch_build_L(const T* C0, const T* R, int k, int s, T* L, const int* status, cudaStream_t st);
+template <typename T>
+void launch_add_diag(T* K, int n, const T* sigma, int k, const int* status, cudaStream_t st);
+size_t jacobi_work_bytes(int n);
+int* jacobi_sweeps_ptr(void* work, int n, int elem);
+template <typename T>
+int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st);
+template <typename T>
+void launch_inverse(const T* W, int k, T* Winv, double thr, int* do_reset, int* status, cudaStream_t st);
+template <typename T>
+void launch_copy(const T* src, T* dst, int64_t count, const int* status, cudaStream_t st);
+template <typename T>
+void launch_commit(T* Wu, const T* Wu_new, const int* reset_u, T* Wv, const T* Wv_new, const int* reset_v,
+                   T* sigma, const T* theta, int k, int64_t* counters, int64_t dm, int64_t dn,
+                   int64_t* resets, int* status, cudaStream_t st);
+template <typename T>
+void launch_check_finite(const T* x, int64_t count, int* status, cudaStream_t st);
+template <typename A, typename B>
+void launch_cast(const A* src, B* dst, int64_t count, cudaStream_t st);
+template <typename T>
+void launch_copy2d(const T* src, int lds, T* dst, int ldd, int rows, int cols, const int* status, cudaStream_t st);
+template <typename T>
+void launch_set_identity(T* W, int k, cudaStream_t st);
+template <typename T> struct FiniteSet {
+  const T* ptr[6];
+  int64_t count[6];
+  int n;
+};
+template <typename T>
+void launch_check_finite_multi(const FiniteSet<T>& set, int* status, cudaStream_t st);
+
+}  // namespace svl

@@ -1,0 +1,198 @@
+"""Torch-side convenience wrapper over the C ABI.
+
+PyTorch provides device memory and streams only: buffers are allocated as
+torch tensors and their pointers are handed to the library; every update
+runs in the library's CUDA kernels.
+"""
+from __future__ import annotations
+
+import ctypes as C
+from dataclasses import dataclass
+from typing import Optional, Tuple
+
+import numpy as np
+import torch
+
+from . import _abi
+from ._abi import check, lib
+
+_STORAGE = {"fp64": _abi.SVLCOV_FP64, "fp32": _abi.SVLCOV_FP32, "bf16": _abi.SVLCOV_BF16}
+_SMALL = {"fp64": _abi.SVLCOV_SMALL_FP64, "fp32": _abi.SVLCOV_SMALL_FP32, "mixed": _abi.SVLCOV_SMALL_MIXED}
+_TORCH_STORAGE = {"fp64": torch.float64, "fp32": torch.float32, "bf16": torch.bfloat16}
+
+
+def _ptr(t: Optional[torch.Tensor]):
+    return None if t is None else C.c_void_p(t.data_ptr())
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return C.c_void_p(s.cuda_stream)
+
+
+@dataclass
+class DeviceCSR:
+    """A batch of update vectors on the device (row j = update vector j)."""
+    indptr: torch.Tensor   # int32, rows + 1
+    indices: torch.Tensor  # int32, nnz
+    values: torch.Tensor   # float32 or float64, nnz
+    rows: int
+    cols: int
+
+    @property
+    def nnz(self) -> int:
+        return int(self.indices.numel())
+
+    def c(self) -> _abi.svlcov_csr:
+        vd = _abi.SVLCOV_FP64 if self.values.dtype == torch.float64 else _abi.SVLCOV_FP32
+        return _abi.svlcov_csr(self.rows, self.cols, self.nnz, self.indptr.data_ptr(),
+                               self.indices.data_ptr() if self.nnz else None,
+                               self.values.data_ptr() if self.nnz else None, vd)
+
+    @staticmethod
+    def from_host(indptr, indices, values, rows: int, cols: int, device="cuda",
+                  values_dtype=torch.float32, non_blocking=False) -> "DeviceCSR":
+        ip = torch.as_tensor(np.asarray(indptr, dtype=np.int32)).to(device, non_blocking=non_blocking)
+        ix = torch.as_tensor(np.asarray(indices, dtype=np.int32)).to(device, non_blocking=non_blocking)
+        vv = torch.as_tensor(np.asarray(values)).to(device=device, dtype=values_dtype, non_blocking=non_blocking)
+        return DeviceCSR(ip, ix, vv, int(rows), int(cols))
+
+
+class SVLCOV:
+    """A rank-k truncated SVD maintained on one GPU (Section 3.2 extended
+    decomposition); see include/svlcov.h for the semantics of each call."""
+
+    def __init__(self, U0: torch.Tensor, sigma0: torch.Tensor, V0: torch.Tensor, *, max_m: int, max_n: int,
+                 max_s: int, max_nnz: int, storage: str = "fp32", small: str = "mixed", tau: float = 0.0,
+                 reset_threshold: float = 0.0, stream=None):
+        assert U0.is_cuda and V0.is_cuda and sigma0.is_cuda
+        m, k = U0.shape
+        n = V0.shape[0]
+        dev = U0.device
+        self.k, self.storage, self.small = int(k), storage, small
+        self.device = dev
+        tdt = _TORCH_STORAGE[storage]
+        self.ubuf = torch.empty((max_m, k), dtype=tdt, device=dev)
+        self.vbuf = torch.empty((max_n, k), dtype=tdt, device=dev)
+        self._U0 = U0.contiguous()
+        self._V0 = V0.contiguous()
+        self._s0 = sigma0.to(torch.float64).contiguous()
+        init_dtype = _abi.SVLCOV_FP64 if U0.dtype == torch.float64 else _abi.SVLCOV_FP32
+        d = _abi.svlcov_init_desc()
+        d.m, d.n, d.k = m, n, k
+        d.max_m, d.max_n, d.max_s, d.max_nnz = max_m, max_n, max_s, max_nnz
+        d.storage, d.small = _STORAGE[storage], _SMALL[small]
+        d.U0, d.sigma0, d.V0, d.init_dtype = self._U0.data_ptr(), self._s0.data_ptr(), self._V0.data_ptr(), init_dtype
+        d.ubuf, d.vbuf = self.ubuf.data_ptr(), self.vbuf.data_ptr()
+        d.tau, d.reset_threshold = tau, reset_threshold
+        nbytes = lib().svlcov_workspace_bytes(C.byref(d))
+        if nbytes == 0:
+            raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_workspace_bytes")
+        self.workspace = torch.empty(nbytes + 256, dtype=torch.uint8, device=dev)
+        base = self.workspace.data_ptr()
+        aligned = (base + 255) & ~255
+        d.workspace, d.workspace_bytes = aligned, nbytes
+        self._desc = d
+        h = C.c_void_p()
+        check(lib().svlcov_init(C.byref(h), C.byref(d), _stream(stream)), "svlcov_init")
+        self.h = h
+
+    def __del__(self):
+        h = getattr(self, "h", None)
+        if h:
+            lib().svlcov_destroy(h)
+            self.h = None
+
+    # ---- updates -------------------------------------------------------------
+    def add_cols(self, batch: DeviceCSR, stream=None):
+        check(lib().svlcov_add_cols(self.h, C.byref(batch.c()), _stream(stream)), "svlcov_add_cols")
+
+    def add_rows(self, batch: DeviceCSR, stream=None):
+        check(lib().svlcov_add_rows(self.h, C.byref(batch.c()), _stream(stream)), "svlcov_add_rows")
+
+    def update_weights(self, D: DeviceCSR, E: DeviceCSR, stream=None):
+        check(lib().svlcov_update_weights(self.h, C.byref(D.c()), C.byref(E.c()), _stream(stream)),
+              "svlcov_update_weights")
+
+    def apply(self, op: str, batch, stream=None):
+        if op == "cols":
+            self.add_cols(batch, stream)
+        elif op == "rows":
+            self.add_rows(batch, stream)
+        else:
+            self.update_weights(batch[0], batch[1], stream)
+
+    # ---- read back -------------------------------------------------------------
+    def shape(self) -> Tuple[int, int, int]:
+        m, n, k = C.c_int64(), C.c_int64(), C.c_int32()
+        check(lib().svlcov_get_shape(self.h, C.byref(m), C.byref(n), C.byref(k)), "svlcov_get_shape")
+        return m.value, n.value, k.value
+
+    def get_factors(self, dtype=torch.float64, stream=None):
+        m, n, k = self.shape()
+        U = torch.empty((m, k), dtype=dtype, device=self.device)
+        V = torch.empty((n, k), dtype=dtype, device=self.device)
+        s = torch.empty(k, dtype=torch.float64, device=self.device)
+        od = _abi.SVLCOV_FP64 if dtype == torch.float64 else _abi.SVLCOV_FP32
+        check(lib().svlcov_get_factors(self.h, _ptr(U), _ptr(s), _ptr(V), od, _stream(stream)), "svlcov_get_factors")
+        return U, s, V
+
+    def query_rows(self, side: int, idx: torch.Tensor, dtype=torch.float64, stream=None) -> torch.Tensor:
+        idx = idx.to(device=self.device, dtype=torch.int32).contiguous()
+        out = torch.empty((idx.numel(), self.k), dtype=dtype, device=self.device)
+        od = _abi.SVLCOV_FP64 if dtype == torch.float64 else _abi.SVLCOV_FP32
+        check(lib().svlcov_query_rows(self.h, side, _ptr(idx), idx.numel(), _ptr(out), od, _stream(stream)),
+              "svlcov_query_rows")
+        return out
+
+    def status(self, stream=None) -> int:
+        code = C.c_int32()
+        check(lib().svlcov_status(self.h, C.byref(code), _stream(stream)), "svlcov_status")
+        return code.value
+
+    def small_state(self, stream=None):
+        k = self.k
+        Wu = np.zeros((k, k)); Wv = np.zeros((k, k)); s = np.zeros(k); r = C.c_int64()
+        check(lib().svlcov_get_small_state(self.h, Wu.ctypes.data_as(C.c_void_p), Wv.ctypes.data_as(C.c_void_p),
+                                           s.ctypes.data_as(C.c_void_p), C.byref(r), _stream(stream)),
+              "svlcov_get_small_state")
+        return Wu, s, Wv, r.value
+
+    def get_state(self, stream=None):
+        m, n, k = self.shape()
+        tdt = {"fp64": np.float64, "fp32": np.float32, "bf16": np.uint16}[self.storage]
+        Up = np.zeros((m, k), dtype=tdt); Vp = np.zeros((n, k), dtype=tdt)
+        Wu = np.zeros((k, k)); Wv = np.zeros((k, k)); s = np.zeros(k)
+        check(lib().svlcov_get_state(self.h, Up.ctypes.data_as(C.c_void_p), Vp.ctypes.data_as(C.c_void_p),
+                                     Wu.ctypes.data_as(C.c_void_p), Wv.ctypes.data_as(C.c_void_p),
+                                     s.ctypes.data_as(C.c_void_p), _stream(stream)), "svlcov_get_state")
+        return dict(m=m, n=n, Up=Up, Vp=Vp, Wu=Wu, Wv=Wv, sigma=s)
+
+    def set_state(self, st: dict, stream=None):
+        arrs = [np.ascontiguousarray(st[x]) for x in ("Up", "Vp", "Wu", "Wv", "sigma")]
+        check(lib().svlcov_set_state(self.h, st["m"], st["n"], *[a.ctypes.data_as(C.c_void_p) for a in arrs],
+                                     _stream(stream)), "svlcov_set_state")
+
+    def intermediate(self, which: int, side: int = 0, stream=None) -> np.ndarray:
+        r, c = C.c_int32(), C.c_int32()
+        check(lib().svlcov_get_intermediate(self.h, which, side, None, 0, C.byref(r), C.byref(c), _stream(stream)),
+              "svlcov_get_intermediate")
+        out = np.zeros(r.value * c.value)
+        check(lib().svlcov_get_intermediate(self.h, which, side, out.ctypes.data_as(C.c_void_p), out.size,
+                                            C.byref(r), C.byref(c), _stream(stream)), "svlcov_get_intermediate")
+        return out.reshape(c.value, r.value).T   # column-major on the device
+
+
+def small_svd(K: torch.Tensor, k: int, precision: str = "fp64", stream=None):
+    """SVD_k of a small dense matrix with the library's Jacobi kernel."""
+    n = K.shape[0]
+    Kc = K.to(torch.float64).t().contiguous()      # column-major
+    F = torch.empty((k, n), dtype=torch.float64, device=K.device)
+    G = torch.empty((k, n), dtype=torch.float64, device=K.device)
+    th = torch.empty(k, dtype=torch.float64, device=K.device)
+    work = torch.empty(lib().svlcov_small_svd_work_bytes(n) + 256, dtype=torch.uint8, device=K.device)
+    wp = (work.data_ptr() + 255) & ~255
+    sweeps = C.c_int32()
+    check(lib().svlcov_small_svd(_ptr(Kc), n, k, _ptr(F), _ptr(th), _ptr(G), _SMALL[precision], C.c_void_p(wp),
+                                 C.byref(sweeps), _stream(stream)), "svlcov_small_svd")
+    return F.t(), th, G.t(), sweeps.value
