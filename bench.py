@@ -1,0 +1,376 @@
+#!/usr/bin/env python
+"""Benchmark of the SV-LCOV update step on GB300.
+
+Workload (the configuration the headline metric is quoted on): graph node
+insertion on a symmetric binary Chung-Lu adjacency matrix, N = 100,000 nodes
+(degree exponent 2.1, mean degree 10), rank k = 64 started from the first
+half of the nodes; the other half arrives in node batches of s = 256, each an
+add-rows step (edges to existing nodes) followed by an add-columns step (edges
+to existing and new nodes).  One benchmark step = one node batch = 512 update
+vectors; the metric is update vectors (columns and rows) per second.
+
+Paths:
+  mixed  (headline) FP32 U'/V', small steps in SVLCOV_SMALL_MIXED
+  plain            FP32 U'/V', small steps in FP32 (SVLCOV_SMALL_FP32)
+Both are timed with CUDA events per step on the launching stream, with the
+batches resident in HBM and the L2 flushed (512 MB write) between steps.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "sparse update cols/s at k=64 (mixed vs plain FP32 GPU); rel err vs FP64 oracle"
+UNIT = "update cols/s"
+WORKLOAD = ("C2 graph node insertion: Chung-Lu N=100000 (gamma 2.1, mean degree 10, binary), k=64, "
+            "node batches of s=256 (add_rows then add_cols)")
+GOLDEN = os.path.join(ROOT, "tests", "golden", "c2_oracle_sigma.json")
+
+
+def parse():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=0, help="timed node batches (0 = all after warm-up)")
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--N", type=int, default=100_000)
+    ap.add_argument("--k", type=int, default=64)
+    ap.add_argument("--s", type=int, default=256)
+    ap.add_argument("--no-plain", action="store_true")
+    ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    return ap.parse_args()
+
+
+def dist_env():
+    rank = int(os.environ.get("RANK", "0"))
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    return rank, world, local
+
+
+def problem(args):
+    return synth.c2_problem(N=args.N, k=args.k, s=args.s)
+
+
+# ---------------------------------------------------------------------------
+class Clocks:
+    """nvidia-smi sampling during the timed region."""
+    Q = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,clocks_event_reasons.hw_slowdown,"
+         "clocks_event_reasons.hw_thermal_slowdown,clocks_event_reasons.sw_thermal_slowdown,"
+         "clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.p = None
+
+    def start(self):
+        try:
+            self.p = subprocess.Popen(["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.Q}",
+                                       "--format=csv,noheader,nounits", "-lms", "200"],
+                                      stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+        except (FileNotFoundError, OSError):
+            self.p = None
+
+    def stop(self):
+        if self.p is None:
+            return dict(sm_mhz=None, sm_max_mhz=None, reasons=["nvidia-smi unavailable"])
+        self.p.terminate()
+        try:
+            out, _ = self.p.communicate(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.p.kill()
+            out, _ = self.p.communicate()
+        sm, mx, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        for line in out.strip().splitlines():
+            f = [x.strip() for x in line.split(",")]
+            if len(f) < 9:
+                continue
+            try:
+                sm.append(float(f[1])); mx.append(float(f[2]))
+            except ValueError:
+                continue
+            for nm, v in zip(names, f[5:9]):
+                if v.lower().startswith("active"):
+                    reasons.add(nm)
+        return dict(sm_mhz=float(np.median(sm)) if sm else None, sm_max_mhz=max(mx) if mx else None,
+                    reasons=sorted(reasons), samples=len(sm))
+
+
+def stage(batches, torch, dev):
+    from paper_2401_09703_gb300 import DeviceCSR
+    out = []
+    for kind, b in batches:
+        out.append((kind, DeviceCSR.from_host(b.indptr, b.indices, b.values, b.rows, b.cols, device=dev,
+                                             values_dtype=torch.float32)))
+    return out
+
+
+def make_handle(p, torch, dev, small, max_s, max_nnz):
+    from paper_2401_09703_gb300 import SVLCOV
+    U = torch.as_tensor(p["U"], dtype=torch.float32, device=dev)
+    V = torch.as_tensor(p["V"], dtype=torch.float32, device=dev)
+    s = torch.as_tensor(p["sigma"], dtype=torch.float64, device=dev)
+    N = p["N"]
+    return SVLCOV(U, s, V, max_m=N + 64, max_n=N + 64, max_s=max_s, max_nnz=max_nnz, storage="fp32", small=small)
+
+
+def run_path(p, dev_batches, torch, dev, small, W, K, flush, profile=False, clocks=None):
+    """Warm-up W node batches, then K timed node batches (events per step on
+    the launching stream, L2 flush between steps outside the events)."""
+    from paper_2401_09703_gb300 import kernel_launches
+    max_s = max(b.rows for _, b in dev_batches)
+    max_nnz = max(b.nnz for _, b in dev_batches)
+    h = make_handle(p, torch, dev, small, max_s, max_nnz)
+    stream = torch.cuda.current_stream()
+    pairs = [(dev_batches[2 * i], dev_batches[2 * i + 1]) for i in range(len(dev_batches) // 2)]
+    for (kr, br), (kc, bc) in pairs[:W]:
+        h.add_rows(br); h.add_cols(bc)
+    torch.cuda.synchronize()
+    if profile:
+        h.profile(True)
+        h.profile_read(reset=True)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+    units = 0
+    if clocks:
+        clocks.start()
+    if torch.distributed.is_initialized():
+        torch.distributed.barrier()
+    torch.cuda.synchronize()
+    l0 = kernel_launches()
+    t0 = time.perf_counter()
+    for i, ((kr, br), (kc, bc)) in enumerate(pairs[W:W + K]):
+        flush.zero_()
+        evs[i][0].record(stream)
+        h.add_rows(br)
+        h.add_cols(bc)
+        evs[i][1].record(stream)
+        units += br.rows + bc.rows
+    torch.cuda.synchronize()
+    wall = time.perf_counter() - t0
+    launches = kernel_launches() - l0
+    ck = clocks.stop() if clocks else None
+    ms = [a.elapsed_time(b) for a, b in evs[:len(pairs[W:W + K])]]
+    code = h.status()
+    prof = h.profile_read() if profile else None
+    U, s, V = h.get_factors(torch.float64)
+    return dict(ms=ms, units=units, wall=wall, status=code, sigma=s.cpu().numpy(), launches=launches, clocks=ck,
+                profile=prof, handle=h, steps=len(ms))
+
+
+def run_e2e(p, batches, torch, dev, W, K):
+    """End to end through the public API with host buffers: every step copies
+    its batches from pinned host memory and reads Sigma back."""
+    from paper_2401_09703_gb300 import DeviceCSR
+    max_s = max(b.rows for _, b in batches)
+    max_nnz = max(b.nnz for _, b in batches)
+    h = make_handle(p, torch, dev, "mixed", max_s, max_nnz)
+    stream = torch.cuda.current_stream()
+    host = []
+    for kind, b in batches:
+        host.append((torch.as_tensor(b.indptr.astype(np.int32)).pin_memory(),
+                     torch.as_tensor(b.indices.astype(np.int32)).pin_memory(),
+                     torch.as_tensor(b.values.astype(np.float32)).pin_memory(), b.rows, b.cols))
+    dip = torch.empty(max_s + 1, dtype=torch.int32, device=dev)
+    dix = torch.empty(max_nnz, dtype=torch.int32, device=dev)
+    dvv = torch.empty(max_nnz, dtype=torch.float32, device=dev)
+    dip2, dix2, dvv2 = torch.empty_like(dip), torch.empty_like(dix), torch.empty_like(dvv)
+    sig_host = torch.empty(h.k, dtype=torch.float64).pin_memory()
+    sig_dev = torch.empty(h.k, dtype=torch.float64, device=dev)
+    from paper_2401_09703_gb300 import _abi
+    import ctypes as C
+
+    def one(i, bufs):
+        ip, ix, vv, rows, cols = host[i]
+        a, b2, c = bufs
+        a[: ip.numel()].copy_(ip, non_blocking=True)
+        b2[: ix.numel()].copy_(ix, non_blocking=True)
+        c[: vv.numel()].copy_(vv, non_blocking=True)
+        return DeviceCSR(a[: ip.numel()], b2[: ix.numel()], c[: vv.numel()], rows, cols), ip.numel() * 4 + ix.numel() * 4 + vv.numel() * 4
+
+    npairs = len(batches) // 2
+    for i in range(W):
+        br, _ = one(2 * i, (dip, dix, dvv)); h.add_rows(br)
+        bc, _ = one(2 * i + 1, (dip2, dix2, dvv2)); h.add_cols(bc)
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    h2d = 0
+    units = 0
+    e0.record(stream)
+    for i in range(W, min(W + K, npairs)):
+        br, nb = one(2 * i, (dip, dix, dvv)); h.add_rows(br); h2d += nb
+        bc, nb = one(2 * i + 1, (dip2, dix2, dvv2)); h.add_cols(bc); h2d += nb
+        _abi.check(_abi.lib().svlcov_get_factors(h.h, None, C.c_void_p(sig_dev.data_ptr()), None, _abi.SVLCOV_FP64,
+                                                 C.c_void_p(stream.cuda_stream)), "get_factors")
+        sig_host.copy_(sig_dev, non_blocking=True)
+        units += br.rows + bc.rows
+    e1.record(stream)
+    torch.cuda.synchronize()
+    steps = max(1, min(W + K, npairs) - W)
+    t = e0.elapsed_time(e1) / 1e3
+    return dict(value=units / t, unit=UNIT, h2d_bytes_per_step=int(h2d / steps), d2h_bytes_per_step=8 * h.k)
+
+
+def roofline_svd(p, prof, small, sweeps_per_launch, n):
+    """The dominant kernel is the Rayleigh-Ritz SVD (one-sided Jacobi).  Its
+    algorithmic work per sweep is n(n-1)/2 rotations x 9n FMA (one dot product
+    and two column-pair updates, of K and of G) = 9 n^2 (n-1) flop."""
+    ms, calls = prof["svd"]
+    per_launch_s = ms / 1e3 / max(calls, 1)
+    flops = sweeps_per_launch * 9.0 * n * n * (n - 1)
+    achieved = flops / per_launch_s / 1e12
+    # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
+    peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    return dict(bound="alu", achieved=round(achieved, 4), peak=round(peak, 2), unit="TFLOP/s",
+                frac=round(achieved / peak, 5), traffic=None, kernel="jacobi (Rayleigh-Ritz SVD_k of K)",
+                flops_per_launch=flops, ms_per_launch=per_launch_s * 1e3,
+                peak_note="FP32 ALU peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz (no measured ALU peak)")
+
+
+def cpu_baseline(p, seconds):
+    """The FP64 oracle (sparse method, as it stands) on the host cores over a
+    bounded prefix of the same trajectory."""
+    from oracle import svlcov as osv
+    st = osv.State.init(p["U"], p["sigma"], p["V"])
+    t0 = time.perf_counter()
+    units = 0
+    nb = 0
+    for kind, b in p["batches"]:
+        st.apply(kind, b)
+        units += b.rows
+        nb += 1
+        if time.perf_counter() - t0 > seconds and nb % 2 == 0:
+            break
+    t = time.perf_counter() - t0
+    cores = len(os.sched_getaffinity(0))
+    return dict(value=units / t, unit=UNIT, cores=cores, kind="oracle",
+                sample=f"first {nb // 2} node batches ({units} update vectors) of the same trajectory, FP64 numpy/scipy")
+
+
+def main_reference(args):
+    rank, world, local = dist_env()
+    if rank != 0:
+        return 0
+    p = problem(args)
+    from oracle import svlcov as osv
+    st = osv.State.init(p["U"], p["sigma"], p["V"])
+    pairs = [(p["batches"][2 * i], p["batches"][2 * i + 1]) for i in range(len(p["batches"]) // 2)]
+    W = min(args.warmup, 1)
+    for (kr, br), (kc, bc) in pairs[:W]:
+        st.apply(kr, br); st.apply(kc, bc)
+    K = args.steps if args.steps > 0 else len(pairs) - W
+    budget = 150.0
+    t0 = time.perf_counter()
+    units, done = 0, 0
+    for (kr, br), (kc, bc) in pairs[W:W + K]:
+        st.apply(kr, br); st.apply(kc, bc)
+        units += br.rows + bc.rows
+        done += 1
+        if time.perf_counter() - t0 > budget:
+            break
+    t = time.perf_counter() - t0
+    v = units / t
+    cores = len(os.sched_getaffinity(0))
+    line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=done, warmup=W,
+                ms_per_step=1e3 * t / max(done, 1), higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f64", data="synthetic", impl="reference",
+                config=dict(workload=WORKLOAD, global_batch=2 * args.s, l2="n/a (CPU)"),
+                cpu_baseline=dict(value=v, unit=UNIT, cores=cores, kind="oracle",
+                                  sample=f"{done} node batches after {W} warm-up (bounded to {budget:.0f} s)"),
+                e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
+    print(json.dumps(line))
+    return 0
+
+
+def main():
+    args = parse()
+    if args.impl == "reference":
+        return main_reference(args)
+    import torch
+    rank, world, local = dist_env()
+    if world > 1:
+        torch.distributed.init_process_group("nccl", device_id=torch.device("cuda", local))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    p = problem(args)
+    npairs = len(p["batches"]) // 2
+    W = max(0, min(args.warmup, npairs - 1))
+    K = args.steps if args.steps > 0 else npairs - W
+    K = max(1, min(K, npairs - W))
+    dev_batches = stage(p["batches"], torch, dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    torch.cuda.synchronize()
+
+    mixed = run_path(p, dev_batches, torch, dev, "mixed", W, K, flush, clocks=Clocks(local))
+    t_mixed = sum(mixed["ms"]) / 1e3
+    plain = None
+    if not args.no_plain:
+        plain = run_path(p, dev_batches, torch, dev, "fp32", W, K, flush)
+    prof = run_path(p, dev_batches, torch, dev, "mixed", W, K, flush, profile=True)
+    e2e = run_e2e(p, p["batches"], torch, dev, W, K)
+
+    # max over ranks of the timed device time
+    t_max = t_mixed
+    if world > 1:
+        tt = torch.tensor([t_mixed], device=dev, dtype=torch.float64)
+        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+        t_max = float(tt.item())
+    value = world * mixed["units"] / t_max
+
+    # accuracy against the stored FP64 oracle trajectory (full default run only)
+    err = dict(mixed=None, plain=None)
+    full = (W + K == npairs) and args.N == 100_000 and args.k == 64 and args.s == 256
+    if full and os.path.exists(GOLDEN):
+        so = np.array(json.load(open(GOLDEN))["sigma_final"])
+        keep = so > 1e-12 * so[0]
+        err["mixed"] = float(np.max(np.abs(mixed["sigma"][keep] - so[keep]) / so[keep]))
+        if plain is not None:
+            err["plain"] = float(np.max(np.abs(plain["sigma"][keep] - so[keep]) / so[keep]))
+
+    line = None
+    if rank == 0:
+        n = args.k + args.s
+        pr = prof["profile"]
+        sweeps = pr["svd_sweeps"] / max(pr["svd"][1], 1)     # average Jacobi sweeps per SVD launch
+        roof = roofline_svd(p, pr, "mixed", sweeps, n)
+        roof["sweeps_per_launch"] = sweeps
+        cpu = None if args.no_cpu else cpu_baseline(p, args.cpu_seconds)
+        phases = {k: dict(ms_total=round(v[0], 3), calls=v[1]) for k, v in prof["profile"].items()
+                  if k != "svd_sweeps"}
+        line = dict(
+            metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=W,
+            ms_per_step=1e3 * t_max / K, higher_is_better=True, scaling="weak", vs_baseline=None,
+            dtype="f32 storage, f32+f64 small steps", data="synthetic",
+            config=dict(workload=WORKLOAD, global_batch=2 * args.s * world, seq_len=None,
+                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                        l2="flushed (512 MB write) between timed steps", mean_degree=p["mean_degree"]),
+            plain_fp32=None if plain is None else dict(value=plain["units"] / (sum(plain["ms"]) / 1e3), unit=UNIT,
+                                                       ms_per_step=sum(plain["ms"]) / len(plain["ms"]),
+                                                       sigma_rel_err_vs_oracle=err["plain"], status=plain["status"]),
+            sigma_rel_err_vs_oracle=err["mixed"], status=mixed["status"],
+            roofline=roof, phases_ms=phases, e2e=e2e, cpu_baseline=cpu,
+            gpu_launches=int(mixed["launches"]), clocks=mixed["clocks"],
+            wall_s_timed_region=mixed["wall"])
+        print(json.dumps(line))
+    if world > 1:
+        torch.distributed.barrier()
+        torch.distributed.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

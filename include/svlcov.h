@@ -181,6 +181,23 @@ int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host
 int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
                             size_t capacity_doubles, int32_t* rows, int32_t* cols, void* stream);
 
+/* Phase timing (the only tracing the library does).  When enabled, every
+ * step records CUDA events on its stream around six phases: 0 validation and
+ * grouping of the batch, 1 gather + Gram (turning into SV-LCOV form, Lemmas
+ * 1-2), 2 CholeskyQR2 of the residual Gram (Algorithm 2), 3 the SVD_k of
+ * the Rayleigh-Ritz matrix, 4 the small folds (Section 3.2), 5 the sparse
+ * addition / append / reset / commit.  svlcov_profile_read synchronises on
+ * the recorded events and returns accumulated milliseconds and counts per
+ * phase (nphases <= 6); *svd_sweeps (may be NULL; synchronises the device)
+ * receives the number of Jacobi sweeps summed over all SVD launches since the
+ * last reset; reset != 0 clears the totals. */
+int svlcov_profile_enable(svlcov_handle* h, int32_t enable);
+int svlcov_profile_read(svlcov_handle* h, double* ms, int64_t* calls, int32_t nphases, int32_t reset,
+                        int64_t* svd_sweeps);
+
+/* Process-wide number of kernels this library has launched so far. */
+uint64_t svlcov_kernel_launches(void);
+
 /* Release the host object (device buffers stay with the caller). */
 void svlcov_destroy(svlcov_handle* h);
 

@@ -60,6 +60,10 @@ SIGNATURES = {
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "svlcov_get_intermediate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
+    "svlcov_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
+    "svlcov_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
+                                      C.POINTER(C.c_int64)]),
+    "svlcov_kernel_launches": (C.c_uint64, []),
     "svlcov_destroy": (None, [C.c_void_p]),
     "svlcov_strerror": (C.c_char_p, [C.c_int32]),
     "svlcov_small_svd_work_bytes": (C.c_size_t, [C.c_int32]),

@@ -40,8 +40,54 @@ int log2_ceil(int64_t v) {
 
 }  // namespace
 
+// Phase timing with CUDA events (enabled by svlcov_profile_enable).
+enum { PH_PREP = 0, PH_GATHER, PH_CHOLQR, PH_SVD, PH_FOLD, PH_APPLY, PH_COUNT };
+
+struct Prof {
+  bool on = false;
+  struct Rec {
+    int ph;
+    cudaEvent_t a, b;
+  };
+  std::vector<Rec> recs;
+  double ms[PH_COUNT] = {};
+  int64_t calls[PH_COUNT] = {};
+  int open = -1;
+  void begin(int ph, cudaStream_t st) {
+    if (!on) return;
+    Rec r{ph, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    cudaEventRecord(r.a, st);
+    recs.push_back(r);
+    open = (int)recs.size() - 1;
+  }
+  void end(cudaStream_t st) {
+    if (!on || open < 0) return;
+    cudaEventRecord(recs[open].b, st);
+    open = -1;
+  }
+  void next(int ph, cudaStream_t st) {
+    end(st);
+    begin(ph, st);
+  }
+  void resolve() {
+    for (auto& r : recs) {
+      float t = 0.f;
+      cudaEventSynchronize(r.b);
+      cudaEventElapsedTime(&t, r.a, r.b);
+      ms[r.ph] += t;
+      calls[r.ph] += 1;
+      cudaEventDestroy(r.a);
+      cudaEventDestroy(r.b);
+    }
+    recs.clear();
+  }
+};
+
 struct svlcov_handle {
   svlcov_init_desc d;
+  Prof prof;
   int64_t m, n;  // host view of the shape
   int k;
   int64_t Hmax;
@@ -49,6 +95,7 @@ struct svlcov_handle {
   int* status;
   int64_t* counters;  // [0] m, [1] n committed
   int64_t* resets;
+  int64_t* stats;     // [0] Jacobi sweeps summed over launches
   int* flags;         // [0] reset_u, [1] reset_v
   double *Wu, *Wv, *sigma;
   // step scratch
@@ -67,6 +114,7 @@ static void layout(svlcov_handle* h, void* base, size_t* total) {
   h->status = c.take<int>(4);
   h->counters = c.take<int64_t>(4);
   h->resets = c.take<int64_t>(2);
+  h->stats = c.take<int64_t>(4);
   h->flags = c.take<int>(8);
   h->Wu = c.take<double>(k * k);
   h->Wv = c.take<double>(k * k);
@@ -192,6 +240,7 @@ extern "C" int svlcov_init(svlcov_handle** out, const svlcov_init_desc* d, void*
   cudaStream_t st = (cudaStream_t)stream;
   cudaMemsetAsync(h->status, 0, sizeof(int) * 4, st);
   cudaMemsetAsync(h->resets, 0, sizeof(int64_t) * 2, st);
+  cudaMemsetAsync(h->stats, 0, sizeof(int64_t) * 4, st);
   cudaMemsetAsync(h->flags, 0, sizeof(int) * 8, st);
   int64_t counters[4] = {d->m, d->n, 0, 0};
   cudaMemcpyAsync(h->counters, counters, sizeof(counters), cudaMemcpyHostToDevice, st);
@@ -209,7 +258,40 @@ extern "C" int svlcov_init(svlcov_handle** out, const svlcov_init_desc* d, void*
   return SVLCOV_OK;
 }
 
-extern "C" void svlcov_destroy(svlcov_handle* h) { delete h; }
+extern "C" void svlcov_destroy(svlcov_handle* h) {
+  if (!h) return;
+  h->prof.resolve();
+  delete h;
+}
+
+extern "C" int svlcov_profile_enable(svlcov_handle* h, int32_t enable) {
+  if (!h) return SVLCOV_ERR_INVALID_ARG;
+  h->prof.on = enable != 0;
+  return SVLCOV_OK;
+}
+
+extern "C" int svlcov_profile_read(svlcov_handle* h, double* ms, int64_t* calls, int32_t nphases, int32_t reset,
+                                   int64_t* svd_sweeps) {
+  if (!h || nphases < 0) return SVLCOV_ERR_INVALID_ARG;
+  h->prof.resolve();
+  if (svd_sweeps) {
+    CUDA_OK(cudaDeviceSynchronize());
+    CUDA_OK(cudaMemcpy(svd_sweeps, h->stats, sizeof(int64_t), cudaMemcpyDeviceToHost));
+    if (reset) CUDA_OK(cudaMemset(h->stats, 0, sizeof(int64_t)));
+  }
+  for (int i = 0; i < nphases && i < PH_COUNT; ++i) {
+    if (ms) ms[i] = h->prof.ms[i];
+    if (calls) calls[i] = h->prof.calls[i];
+  }
+  if (reset)
+    for (int i = 0; i < PH_COUNT; ++i) {
+      h->prof.ms[i] = 0.0;
+      h->prof.calls[i] = 0;
+    }
+  return SVLCOV_OK;
+}
+
+extern "C" uint64_t svlcov_kernel_launches(void) { return launches_total(); }
 
 // ---------------------------------------------------------------------------
 // One side of Algorithm 2 in the CholeskyQR2 form: from the batch, the
@@ -221,11 +303,14 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
                           cudaStream_t st) {
   int k = h->k, s = b.rows;
   int* status = h->status;
+  h->prof.begin(PH_PREP, st);
   launch_validate(b, d_len, sb.sc.rowid, status, st);
   int logH = std::max(4, log2_ceil(2 * std::max<int64_t>(b.nnz, 1)));
   launch_group(b, logH, sb.sc, status, st);
   TC *P = (TC*)sb.P, *SE = (TC*)sb.SE, *C0 = (TC*)sb.C0, *e2 = (TC*)sb.e2;
+  h->prof.next(PH_GATHER, st);
   launch_gather_gram<TS, TC>(b, Xp, k, W, sb.sc, P, SE, C0, e2, status, st);
+  h->prof.next(PH_CHOLQR, st);
   TC *S = (TC*)sb.S, *L1 = (TC*)sb.L1, *Y1 = (TC*)sb.Y1, *T1 = (TC*)sb.T1, *S2 = (TC*)sb.S2;
   TC *L2 = (TC*)sb.L2, *Y2 = (TC*)sb.Y2, *R = (TC*)sb.R, *X = (TC*)sb.X, *CQ = (TC*)sb.CQ;
   launch_copy<TC>(SE, S, (int64_t)s * s, status, st);
@@ -240,6 +325,7 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
   gemm<TC>(true, true, s, s, s, (TC)1, L2, s, L1, s, (TC)0, R, s, status, st);           // R = L2^T L1^T
   gemm<TC>(true, true, s, s, s, (TC)1, Y1, s, Y2, s, (TC)0, X, s, status, st);           // X = Y1^T Y2^T
   gemm<TC>(false, false, k, s, s, (TC)1, C0, k, X, s, (TC)0, CQ, k, status, st);         // C_Q = C0 X
+  h->prof.end(st);
 }
 
 // Fold of one projected side (Section 3.2): Xn = W (Fk - C_Q Fs), Winv, and
@@ -276,9 +362,11 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   int64_t rowsP = cols ? h->m : h->n, rowsO = cols ? h->n : h->m;
   orthogonalise<TS, TC>(h, b, rowsP, XpP, WP, sb, st);
   TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
+  h->prof.begin(PH_SVD, st);
   launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
-  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st);               // F, Theta, G = SVD_k(K)
+  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st, h->stats);               // F, Theta, G = SVD_k(K)
   if (e) return SVLCOV_ERR_CUDA;
+  h->prof.next(PH_FOLD, st);
   fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, st);
   gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, st);      // W_O G[:k]
   launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st);
@@ -290,6 +378,7 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   fs.ptr[3] = WPn; fs.count[3] = (int64_t)k * k;
   fs.ptr[4] = WOn; fs.count[4] = (int64_t)k * k;
   fs.n = 5;
+  h->prof.next(PH_APPLY, st);
   launch_check_finite_multi<TC>(fs, status, st);
   launch_reset<TS, TC>(XpP, rowsP, k, WPn, rP, status, st);   // only when the guard fired
   launch_scatter<TS, TC>(XpP, k, (TC*)sb.Mt, b.nnz, sb.sc, status, st);
@@ -301,6 +390,7 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   else
     launch_commit<TC>((TC*)h->Wu, WOn, rO, (TC*)h->Wv, WPn, rP, (TC*)h->sigma, theta, k, h->counters, s, 0,
                       h->resets, status, st);
+  h->prof.end(st);
   return last_launch();
 }
 
@@ -313,12 +403,14 @@ static int step_weights(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr&
   orthogonalise<TS, TC>(h, D, h->m, (TS*)h->d.ubuf, (TC*)h->Wu, sd, st);
   orthogonalise<TS, TC>(h, E, h->n, (TS*)h->d.vbuf, (TC*)h->Wv, se, st);
   TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
+  h->prof.begin(PH_SVD, st);
   launch_build_L<TC>((TC*)sd.C0, (TC*)sd.R, k, s, (TC*)sd.Lm, status, st);
   launch_build_L<TC>((TC*)se.C0, (TC*)se.R, k, s, (TC*)se.Lm, status, st);
   gemm<TC>(false, true, n2, n2, s, (TC)1, (TC*)sd.Lm, n2, (TC*)se.Lm, n2, (TC)0, K, n2, status, st);
   launch_add_diag<TC>(K, n2, (TC*)h->sigma, k, status, st);   // K = diag(S,0) + [C0D;RD][C0E;RE]^T
-  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st);
+  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st, h->stats);
   if (e) return SVLCOV_ERR_CUDA;
+  h->prof.next(PH_FOLD, st);
   fold_projected<TC>(h, sd, (TC*)h->Wu, F, n2, s, (TC*)h->Xu, (TC*)h->Wu_new, (TC*)h->Wu_inv, h->flags + 0, st);
   fold_projected<TC>(h, se, (TC*)h->Wv, G, n2, s, (TC*)h->Xv, (TC*)h->Wv_new, (TC*)h->Wv_inv, h->flags + 1, st);
   FiniteSet<TC> fs{};
@@ -328,6 +420,7 @@ static int step_weights(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr&
   fs.ptr[3] = (TC*)h->Wu_new; fs.count[3] = (int64_t)k * k;
   fs.ptr[4] = (TC*)h->Wv_new; fs.count[4] = (int64_t)k * k;
   fs.n = 5;
+  h->prof.next(PH_APPLY, st);
   launch_check_finite_multi<TC>(fs, status, st);
   launch_reset<TS, TC>((TS*)h->d.ubuf, h->m, k, (TC*)h->Wu_new, h->flags + 0, status, st);
   launch_scatter<TS, TC>((TS*)h->d.ubuf, k, (TC*)sd.Mt, D.nnz, sd.sc, status, st);
@@ -335,6 +428,7 @@ static int step_weights(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr&
   launch_scatter<TS, TC>((TS*)h->d.vbuf, k, (TC*)se.Mt, E.nnz, se.sc, status, st);
   launch_commit<TC>((TC*)h->Wu, (TC*)h->Wu_new, h->flags + 0, (TC*)h->Wv, (TC*)h->Wv_new, h->flags + 1,
                     (TC*)h->sigma, theta, k, h->counters, 0, 0, h->resets, status, st);
+  h->prof.end(st);
   return last_launch();
 }
 

@@ -30,6 +30,11 @@ struct SideScratch {
 
 int64_t max_chunks(int64_t max_s, int64_t max_nnz);
 
+// Process-wide count of kernels launched by the library (a diagnostic for
+// benchmarks: how many of this library's kernels ran in a timed region).
+void note_launches(int n);
+uint64_t launches_total();
+
 // ---- sparse side (templated on storage TS and small-step type TC) ----------
 void launch_validate(const svlcov_csr& b, int64_t d, int* rowid, int* status, cudaStream_t st);
 void launch_group(const svlcov_csr& b, int logH, const SideScratch& w, int* status, cudaStream_t st);
@@ -71,7 +76,8 @@ void launch_add_diag(T* K, int n, const T* sigma, int k, const int* status, cuda
 size_t jacobi_work_bytes(int n);
 int* jacobi_sweeps_ptr(void* work, int n, int elem);
 template <typename T>
-int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st);
+int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st,
+                  int64_t* sweep_total = nullptr);
 template <typename T>
 void launch_inverse(const T* W, int k, T* Winv, double thr, int* do_reset, int* status, cudaStream_t st);
 template <typename T>

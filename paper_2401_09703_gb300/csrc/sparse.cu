@@ -5,9 +5,15 @@
 // matrix addition that folds B F[k:] U''^-1 into U' (Section 3.2), the row
 // append, the identity reset of the extended decomposition, and the
 // materialisation / query U = U' U'' (Theorem 1, Query).
+#include <atomic>
+
 #include "kernels.cuh"
 
 namespace svl {
+
+static std::atomic<uint64_t> g_launches{0};
+void note_launches(int n) { g_launches.fetch_add((uint64_t)n, std::memory_order_relaxed); }
+uint64_t launches_total() { return g_launches.load(std::memory_order_relaxed); }
 
 int64_t max_chunks(int64_t max_s, int64_t max_nnz) { return max_s + max_nnz / kChunk + 1; }
 
@@ -48,6 +54,7 @@ __global__ void k_validate(const int32_t* __restrict__ indptr, const int32_t* __
 void launch_validate(const svlcov_csr& b, int64_t d, int* rowid, int* status, cudaStream_t st) {
   if (b.rows <= 0) return;
   int wpb = 8;
+  note_launches(1);
   k_validate<<<(int)cdiv(b.rows, wpb), wpb * 32, 0, st>>>(b.indptr, b.indices, b.values, b.values_dtype,
                                                          b.rows, d, b.nnz, rowid, status);
 }
@@ -185,19 +192,31 @@ __global__ void k_group_rank(const int* __restrict__ tmp_j, const int* __restric
   seg_v[st + r] = load_val<double>(values, vdtype, e);
 }
 
+__global__ void k_hash_clear(int* __restrict__ hkey, int* __restrict__ hcnt, int H) {
+  int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t < H) {
+    hkey[t] = -1;
+    hcnt[t] = 0;
+  }
+}
+
 void launch_group(const svlcov_csr& b, int logH, const SideScratch& w, int* status, cudaStream_t st) {
   int H = 1 << logH;
-  cudaMemsetAsync(w.hkey, 0xff, sizeof(int) * H, st);
-  cudaMemsetAsync(w.hcnt, 0, sizeof(int) * H, st);
+  note_launches(1);
+  k_hash_clear<<<(int)cdiv(H, 256), 256, 0, st>>>(w.hkey, w.hcnt, H);
   int64_t nnz = b.nnz;
   if (nnz > 0)
+    note_launches(1);
     k_hash_insert<<<(int)cdiv(nnz, 256), 256, 0, st>>>(b.indices, nnz, logH, w.hkey, w.hcnt, w.slot,
                                                        w.rank_tmp, status);
+  note_launches(1);
   k_group_scan<<<1, 1024, 0, st>>>(w.hcnt, H, w.hstart, w.occ, b.indptr, b.rows, w.chunk_off, w.chunk_row,
                                    w.counts, status);
   if (nnz > 0) {
+    note_launches(1);
     k_group_fill<<<(int)cdiv(nnz, 256), 256, 0, st>>>(w.slot, w.rank_tmp, w.hstart, w.rowid, nnz, w.tmp_j,
                                                       w.tmp_e, status);
+    note_launches(1);
     k_group_rank<<<(int)cdiv(nnz, 256), 256, 0, st>>>(w.tmp_j, w.tmp_e, w.slot, w.hstart, w.hcnt, b.values,
                                                       b.values_dtype, nnz, w.seg_j, w.seg_v, status);
   }
@@ -305,12 +324,14 @@ void launch_gather_gram(const svlcov_csr& b, const TS* Xp, int k, const TC* W, c
   {                                                                                                           \
     auto fn = k_gather_gram<TS, KV>;                                                                          \
     if (smem > 48 * 1024) cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);  \
+    note_launches(1);                                                                                          \
     fn<<<grid, wpb * 32, smem, st>>>(b.indptr, b.indices, b.values, b.values_dtype, s, Xp, k, w.chunk_off,    \
                                      w.chunk_row, w.counts, w.slot, w.hstart, w.hcnt, w.seg_j, w.seg_v,       \
                                      (A*)w.Ppart, w.SEpart, status);                                          \
   }
   if (kv <= 1) GG_LAUNCH(1) else if (kv == 2) GG_LAUNCH(2) else if (kv == 3) GG_LAUNCH(3) else GG_LAUNCH(4)
 #undef GG_LAUNCH
+  note_launches(1);
   k_reduce_c0<A, TC><<<s, 128, 0, st>>>((const A*)w.Ppart, w.SEpart, w.chunk_off, s, k, W, P, SE, C0, e2, status);
 }
 
@@ -360,8 +381,11 @@ void launch_scatter(TS* Xp, int k, const TC* Mt, int64_t nnz, const SideScratch&
   int grid = (int)cdiv(nnz, wpb);
   int kv = (k + 31) / 32;
 #define SC_LAUNCH(KV)                                                                                          \
-  k_scatter<TS, TC, KV><<<grid, wpb * 32, 0, st>>>(Xp, k, Mt, w.occ, w.counts, w.hkey, w.hstart, w.hcnt, w.seg_j, \
-                                                   w.seg_v, status);
+  {                                                                                                            \
+    note_launches(1);                                                                                          \
+    k_scatter<TS, TC, KV><<<grid, wpb * 32, 0, st>>>(Xp, k, Mt, w.occ, w.counts, w.hkey, w.hstart, w.hcnt,     \
+                                                     w.seg_j, w.seg_v, status);                                \
+  }
   if (kv <= 1) SC_LAUNCH(1) else if (kv == 2) SC_LAUNCH(2) else if (kv == 3) SC_LAUNCH(3) else SC_LAUNCH(4)
 #undef SC_LAUNCH
 }
@@ -381,6 +405,7 @@ template <typename TS, typename TC>
 void launch_append(TS* Xp, int64_t row0, int k, int s, const TC* Nt, const int* status, cudaStream_t st) {
   if (s <= 0) return;
   int64_t n = (int64_t)s * k;
+  note_launches(1);
   k_append<TS, TC><<<(int)cdiv(n, 256), 256, 0, st>>>(Xp, row0, k, s, Nt, status);
 }
 
@@ -431,6 +456,7 @@ void launch_reset(TS* Xp, int64_t rows, int k, const TC* Wn, const int* do_reset
   auto fn = k_rowmul<TS, TC, TS>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = (int)std::min<int64_t>(cdiv(rows, nw), 152 * 4);
+  note_launches(1);
   fn<<<grid, nw * 32, smem, st>>>(Xp, rows, k, Wn, Xp, nullptr, rows, do_reset, status, nullptr);
 }
 
@@ -444,10 +470,12 @@ void launch_materialize(const TS* Xp, int64_t rows, int64_t src_rows, int k, con
   if (out_dtype == SVLCOV_FP64) {
     auto fn = k_rowmul<TS, TC, double>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launches(1);
     fn<<<grid, nw * 32, smem, st>>>(Xp, rows, k, W, (double*)out, idx, src_rows, nullptr, nullptr, err);
   } else {
     auto fn = k_rowmul<TS, TC, float>;
     cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    note_launches(1);
     fn<<<grid, nw * 32, smem, st>>>(Xp, rows, k, W, (float*)out, idx, src_rows, nullptr, nullptr, err);
   }
 }
@@ -463,6 +491,7 @@ __global__ void k_convert_in(const void* __restrict__ src, int src_dtype, TS* __
 template <typename TS>
 void launch_convert_in(const void* src, int src_dtype, TS* dst, int64_t count, cudaStream_t st) {
   if (count <= 0) return;
+  note_launches(1);
   k_convert_in<TS><<<(int)cdiv(count, 256), 256, 0, st>>>(src, src_dtype, dst, count);
 }
 

@@ -173,6 +173,19 @@ class SVLCOV:
         check(lib().svlcov_set_state(self.h, st["m"], st["n"], *[a.ctypes.data_as(C.c_void_p) for a in arrs],
                                      _stream(stream)), "svlcov_set_state")
 
+    PHASES = ("prep", "gather_gram", "cholqr2", "svd", "fold", "apply")
+
+    def profile(self, enable: bool = True):
+        check(lib().svlcov_profile_enable(self.h, 1 if enable else 0), "svlcov_profile_enable")
+
+    def profile_read(self, reset: bool = True) -> dict:
+        ms = np.zeros(6); calls = np.zeros(6, dtype=np.int64); sw = C.c_int64()
+        check(lib().svlcov_profile_read(self.h, ms.ctypes.data_as(C.c_void_p), calls.ctypes.data_as(C.c_void_p), 6,
+                                        1 if reset else 0, C.byref(sw)), "svlcov_profile_read")
+        out = {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(self.PHASES)}
+        out["svd_sweeps"] = int(sw.value)
+        return out
+
     def intermediate(self, which: int, side: int = 0, stream=None) -> np.ndarray:
         r, c = C.c_int32(), C.c_int32()
         check(lib().svlcov_get_intermediate(self.h, which, side, None, 0, C.byref(r), C.byref(c), _stream(stream)),
@@ -181,6 +194,10 @@ class SVLCOV:
         check(lib().svlcov_get_intermediate(self.h, which, side, out.ctypes.data_as(C.c_void_p), out.size,
                                             C.byref(r), C.byref(c), _stream(stream)), "svlcov_get_intermediate")
         return out.reshape(c.value, r.value).T   # column-major on the device
+
+
+def kernel_launches() -> int:
+    return int(lib().svlcov_kernel_launches())
 
 
 def small_svd(K: torch.Tensor, k: int, precision: str = "fp64", stream=None):
