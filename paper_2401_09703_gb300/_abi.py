@@ -21,6 +21,7 @@ SVLCOV_FP64, SVLCOV_FP32, SVLCOV_BF16 = 0, 1, 2
 SVLCOV_SMALL_FP64, SVLCOV_SMALL_FP32, SVLCOV_SMALL_MIXED = 0, 1, 2
 SVLCOV_MAX_K = 128
 SVLCOV_MAX_S = 1024
+SVLCOV_SMALL_SVD_STATIC_MAX_N = 256
 
 
 class svlcov_csr(C.Structure):
@@ -69,6 +70,8 @@ SIGNATURES = {
     "svlcov_small_svd_work_bytes": (C.c_size_t, [C.c_int32]),
     "svlcov_small_svd": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+    "svlcov_small_svd_static": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
+                                          C.c_int32, C.POINTER(C.c_int32), C.c_void_p]),
 }
 
 _LIB = None

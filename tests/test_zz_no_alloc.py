@@ -1,0 +1,64 @@
+"""The allocation-free small SVD (svlcov_small_svd_static) against the
+workspace version (svlcov_small_svd), through the C ABI.
+
+It serves callers that may not call cudaMalloc (code under another
+component's caching allocator, or latency-sensitive code where an allocation
+would synchronise the device); its scratch is a fixed array inside the
+library.  This file is collected last so that a run stopping at the first
+failure has already run every other test; it also passes on its own in a
+fresh process."""
+import ctypes as C
+
+import numpy as np
+import pytest
+
+import synth
+from oracle import dense
+
+torch = pytest.importorskip("torch")
+
+
+def _call_static(Kt, k, precision):
+    from paper_2401_09703_gb300 import _abi
+    L = _abi.lib()
+    n = Kt.shape[0]
+    Kc = Kt.to(torch.float64).t().contiguous()
+    F = torch.empty((k, n), dtype=torch.float64, device=Kt.device)
+    G = torch.empty((k, n), dtype=torch.float64, device=Kt.device)
+    th = torch.empty(k, dtype=torch.float64, device=Kt.device)
+    sweeps = C.c_int32()
+    stream = C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    rc = L.svlcov_small_svd_static(C.c_void_p(Kc.data_ptr()), n, k, C.c_void_p(F.data_ptr()),
+                                   C.c_void_p(th.data_ptr()), C.c_void_p(G.data_ptr()), precision,
+                                   C.byref(sweeps), stream)
+    return rc, F.t().cpu().numpy(), th.cpu().numpy(), G.t().cpu().numpy(), sweeps.value
+
+
+def test_static_rejects_oversize_without_cuda():
+    """Runs on CPU too: the size check comes before any CUDA call."""
+    from paper_2401_09703_gb300 import _abi
+    L = _abi.lib()
+    dummy = C.c_void_p(16)
+    rc = L.svlcov_small_svd_static(dummy, _abi.SVLCOV_SMALL_SVD_STATIC_MAX_N + 1, 4, dummy, dummy, dummy,
+                                   _abi.SVLCOV_SMALL_FP64, None, None)
+    assert rc == _abi.SVLCOV_ERR_CAPACITY
+
+
+@pytest.mark.gpu
+@pytest.mark.parametrize("precision,tol", [(0, 1e-12), (1, 2e-5)])
+def test_static_matches_workspace_version_two_calls(precision, tol):
+    from paper_2401_09703_gb300 import _abi, small_svd
+    g = synth.rng(2024 + precision)
+    for n, k in [(200, 40), (96, 24)]:            # two calls in a row, sizes differ
+        K = np.triu(g.standard_normal((n, n)))
+        K[:k, :k] = np.diag(np.sort(np.abs(g.standard_normal(k)))[::-1] * 4)
+        Kt = torch.as_tensor(K, device="cuda")
+        rc, F, th, G, sw = _call_static(Kt, k, precision)
+        assert rc == _abi.SVLCOV_OK
+        Fw, thw, Gw, sww = small_svd(Kt, k, {0: "fp64", 1: "fp32"}[precision])
+        Fw, thw, Gw = Fw.cpu().numpy(), thw.cpu().numpy(), Gw.cpu().numpy()
+        assert np.max(np.abs(th - thw) / thw) < tol
+        assert np.max(np.abs(F @ F.T - Fw @ Fw.T)) < 100 * tol
+        assert np.max(np.abs(G @ G.T - Gw @ Gw.T)) < 100 * tol
+        _, tho, _ = dense.svd_k(K, k)
+        assert np.max(np.abs(th - tho) / tho) < tol
