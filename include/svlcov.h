@@ -209,8 +209,11 @@ const char* svlcov_strerror(int32_t code);
 /* Rank-k SVD of a small dense matrix (the Rayleigh-Ritz step of Section 2.1,
  * SVD_k of K): one-sided Jacobi.  K: device, n x n column-major FP64 (not
  * modified).  F (n x k), theta (k), G (n x k): device FP64 outputs,
- * column-major, theta descending.  precision: SVLCOV_SMALL_*.  work: device
- * scratch of svlcov_small_svd_work_bytes(n) bytes.  Returns the number of
+ * column-major, theta descending.  precision: SVLCOV_SMALL_FP64 (FP64
+ * sweeps), SVLCOV_SMALL_FP32 (FP32 sweeps on K rounded to FP32) or
+ * SVLCOV_SMALL_MIXED (FP32 sweeps, then one FP64 first-order refinement of
+ * the leading k triplets built from GEMMs).  work: device scratch of
+ * svlcov_small_svd_work_bytes(n) bytes.  Returns the number of
  * sweeps in *sweeps (host, may be NULL; synchronises when non-NULL). */
 size_t svlcov_small_svd_work_bytes(int32_t n);
 int svlcov_small_svd(const double* K, int32_t n, int32_t k, double* F, double* theta, double* G,

@@ -102,6 +102,7 @@ struct svlcov_handle {
   SideBufs side[2];
   double *K, *F, *G, *theta, *Xu, *Xv, *Wu_new, *Wv_new, *Wu_inv, *Wv_inv, *Nt;
   void* jwork;
+  void* rwork;  // FP64 refinement scratch of the mixed SVD
   // bookkeeping of the last step
   int last_op = -1, last_s = 0;
 };
@@ -169,6 +170,7 @@ static void layout(svlcov_handle* h, void* base, size_t* total) {
   h->Wv_inv = c.take<double>(k * k);
   h->Nt = c.take<double>(k * s);
   h->jwork = c.take<char>(jacobi_work_bytes((int)n2));
+  h->rwork = c.take<char>(d.small == SVLCOV_SMALL_MIXED ? refine_work_bytes((int)n2, (int)k) : 256);
   *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -343,6 +345,16 @@ static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
 
+// SVD_k of the Rayleigh-Ritz matrix: Jacobi in the small-step precision, or
+// FP32 sweeps + FP64 refinement in the mixed mode.
+template <typename TC>
+static int small_svd_step(svlcov_handle* h, const TC* K, int n2, TC* F, TC* theta, TC* G, cudaStream_t st) {
+  if (h->d.small == SVLCOV_SMALL_MIXED)
+    return launch_mixed_svd((const double*)K, n2, h->k, (double*)F, (double*)theta, (double*)G, h->jwork, h->rwork,
+                            h->status, st, h->stats);
+  return launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats);
+}
+
 template <typename TS, typename TC>
 static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream_t st) {
   int k = h->k, s = b.rows, n2 = k + s;
@@ -364,7 +376,7 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
   h->prof.begin(PH_SVD, st);
   launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
-  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st, h->stats);               // F, Theta, G = SVD_k(K)
+  int e = small_svd_step<TC>(h, K, n2, F, theta, G, st);                                  // F, Theta, G = SVD_k(K)
   if (e) return SVLCOV_ERR_CUDA;
   h->prof.next(PH_FOLD, st);
   fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, st);
@@ -408,7 +420,7 @@ static int step_weights(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr&
   launch_build_L<TC>((TC*)se.C0, (TC*)se.R, k, s, (TC*)se.Lm, status, st);
   gemm<TC>(false, true, n2, n2, s, (TC)1, (TC*)sd.Lm, n2, (TC*)se.Lm, n2, (TC)0, K, n2, status, st);
   launch_add_diag<TC>(K, n2, (TC*)h->sigma, k, status, st);   // K = diag(S,0) + [C0D;RD][C0E;RE]^T
-  int e = launch_jacobi<TC>(K, n2, k, F, theta, G, h->jwork, status, st, h->stats);
+  int e = small_svd_step<TC>(h, K, n2, F, theta, G, st);
   if (e) return SVLCOV_ERR_CUDA;
   h->prof.next(PH_FOLD, st);
   fold_projected<TC>(h, sd, (TC*)h->Wu, F, n2, s, (TC*)h->Xu, (TC*)h->Wu_new, (TC*)h->Wu_inv, h->flags + 0, st);
@@ -701,7 +713,8 @@ extern "C" const char* svlcov_strerror(int32_t code) {
 // ---- standalone small SVD ----------------------------------------------------
 extern "C" size_t svlcov_small_svd_work_bytes(int32_t n) {
   if (n <= 0) return 0;
-  return jacobi_work_bytes(n) + 3 * (size_t)n * n * sizeof(double) + 2 * n * sizeof(double) + 4096;
+  return jacobi_work_bytes(n) + 3 * (size_t)n * n * sizeof(double) + 2 * n * sizeof(double) +
+         refine_work_bytes(n, n) + 8192;
 }
 
 extern "C" int svlcov_small_svd(const double* K, int32_t n, int32_t k, double* F, double* theta, double* G,
@@ -723,13 +736,16 @@ extern "C" int svlcov_small_svd(const double* K, int32_t n, int32_t k, double* F
     launch_cast<float, double>(Ff, F, (int64_t)n * k, st);
     launch_cast<float, double>(Gf, G, (int64_t)n * k, st);
     launch_cast<float, double>(tf, theta, k, st);
+  } else if (precision == SVLCOV_SMALL_MIXED) {
+    char* rw = c.take<char>(refine_work_bytes(n, k));
+    e = launch_mixed_svd(K, n, k, F, theta, G, jw, rw, status, st, nullptr);
   } else {
     e = launch_jacobi<double>(K, n, k, F, theta, G, jw, status, st);
   }
   if (e) return SVLCOV_ERR_CUDA;
   if (sweeps) {
     CUDA_OK(cudaStreamSynchronize(st));
-    int* sw = jacobi_sweeps_ptr(jw, n, precision == SVLCOV_SMALL_FP32 ? 4 : 8);
+    int* sw = jacobi_sweeps_ptr(jw, n, precision == SVLCOV_SMALL_FP64 ? 8 : 4);
     CUDA_OK(cudaMemcpy(sweeps, sw, sizeof(int), cudaMemcpyDeviceToHost));
   }
   return last_launch();

@@ -75,6 +75,9 @@ template <typename T>
 void launch_add_diag(T* K, int n, const T* sigma, int k, const int* status, cudaStream_t st);
 size_t jacobi_work_bytes(int n);
 int* jacobi_sweeps_ptr(void* work, int n, int elem);
+size_t refine_work_bytes(int n, int k);
+int launch_mixed_svd(const double* K, int n, int k, double* F, double* theta, double* G, void* jwork, void* rwork,
+                     int* status, cudaStream_t st, int64_t* sweep_total);
 template <typename T>
 int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st,
                   int64_t* sweep_total = nullptr);
