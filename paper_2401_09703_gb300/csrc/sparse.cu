@@ -418,12 +418,14 @@ template <typename TS, typename TC, typename TO>
 __global__ void k_rowmul(const TS* __restrict__ Xp, int64_t rows, int k, const TC* __restrict__ W,
                          TO* __restrict__ out, const int32_t* __restrict__ idx, int64_t src_rows,
                          const int* do_reset, const int* status, int* err) {
-  extern __shared__ double wsm[];
+  using A = typename Acc<TS>::type;  // FP32 math for FP32/BF16 storage, FP64 for FP64 storage
+  extern __shared__ __align__(16) unsigned char rm_smem[];
+  A* wsm = (A*)rm_smem;
   if (do_reset && *(volatile const int*)do_reset == 0) return;
   if (status && failed(status)) return;
   int nw = blockDim.x >> 5, wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) wsm[t] = (double)W[t];
-  double* xrow = wsm + k * k + wib * kMaxK;
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) wsm[t] = (A)W[t];
+  A* xrow = wsm + k * k + wib * kMaxK;
   __syncthreads();
   for (int64_t r = (int64_t)blockIdx.x * nw + wib; r < rows; r += (int64_t)gridDim.x * nw) {
     int64_t src = r;
@@ -435,13 +437,13 @@ __global__ void k_rowmul(const TS* __restrict__ Xp, int64_t rows, int k, const T
         continue;
       }
     }
-    for (int a = lane; a < k; a += 32) xrow[a] = to_f64(Xp[src * k + a]);
+    for (int a = lane; a < k; a += 32) xrow[a] = (A)to_f64(Xp[src * k + a]);
     __syncwarp();
     for (int a = lane; a < k; a += 32) {
-      double sum = 0.0;
-      const double* wa = wsm + (int64_t)a * k;
-      for (int b2 = 0; b2 < k; ++b2) sum += xrow[b2] * wa[b2];
-      out[r * k + a] = from_f64<TO>(sum);
+      A sum = (A)0;
+      const A* wa = wsm + (int64_t)a * k;
+      for (int b2 = 0; b2 < k; ++b2) sum = fma(xrow[b2], wa[b2], sum);
+      out[r * k + a] = from_f64<TO>((double)sum);
     }
     __syncwarp();
   }
@@ -452,7 +454,7 @@ void launch_reset(TS* Xp, int64_t rows, int k, const TC* Wn, const int* do_reset
                   cudaStream_t st) {
   if (rows <= 0) return;
   int nw = 8;
-  size_t smem = sizeof(double) * ((size_t)k * k + nw * kMaxK);
+  size_t smem = sizeof(typename Acc<TS>::type) * ((size_t)k * k + nw * kMaxK);
   auto fn = k_rowmul<TS, TC, TS>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
   int grid = (int)std::min<int64_t>(cdiv(rows, nw), 152 * 4);
@@ -465,7 +467,7 @@ void launch_materialize(const TS* Xp, int64_t rows, int64_t src_rows, int k, con
                         int out_dtype, const int32_t* idx, cudaStream_t st, int* err) {
   if (rows <= 0) return;
   int nw = 8;
-  size_t smem = sizeof(double) * ((size_t)k * k + nw * kMaxK);
+  size_t smem = sizeof(typename Acc<TS>::type) * ((size_t)k * k + nw * kMaxK);
   int grid = (int)std::min<int64_t>(cdiv(rows, nw), 152 * 8);
   if (out_dtype == SVLCOV_FP64) {
     auto fn = k_rowmul<TS, TC, double>;

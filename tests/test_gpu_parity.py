@@ -51,8 +51,10 @@ def test_small_svd_matches_lapack(n, k, precision, tol):
     Fo, tho, Go = dense.svd_k(K, k)
     assert checks.sigma_rel_err(th, tho) < tol
     kp = checks.gapped_prefix(tho, 1e-3)
-    assert checks.max_sin_angle(F[:, :kp], Fo[:, :kp]) < 100 * tol
-    assert checks.max_sin_angle(G[:, :kp], Go[:, :kp]) < 100 * tol
+    # vectors of pairs 1e-3 * sigma_1 apart: FP32 sweeps leave ~eps32 sqrt(n) / 1e-3
+    vtol = 1e-2 if precision == "fp32" else 100 * tol
+    assert checks.max_sin_angle(F[:, :kp], Fo[:, :kp]) < vtol
+    assert checks.max_sin_angle(G[:, :kp], Go[:, :kp]) < vtol
     assert np.max(np.abs(K @ G - F * th)) < 10 * tol * th[0]
     assert 0 < sweeps < 40
 
