@@ -56,9 +56,15 @@ template <typename TS>
 void launch_convert_in(const void* src, int src_dtype, TS* dst, int64_t count, cudaStream_t st);
 
 // ---- dense small steps (templated on TC) -----------------------------------
+// tri (optional): 1 op(A) upper, 2 op(A) lower, 4 op(B) upper, 8 op(B) lower triangular
 template <typename T>
 void gemm(bool ta, bool tb, int M, int N, int Kd, T alpha, const T* A, int lda, const T* B, int ldb,
-          T beta, T* C, int ldc, const int* status, cudaStream_t st);
+          T beta, T* C, int ldc, const int* status, cudaStream_t st, int tri = 0);
+enum { TRI_A_UP = 1, TRI_A_LO = 2, TRI_B_UP = 4, TRI_B_LO = 8 };
+size_t cholinv_smem_bytes(int s, size_t elem);
+template <typename T, typename SrcT, typename OutT, bool DELTA>
+bool launch_cholinv_smem(const SrcT* S, int s, const SrcT* ref, T tau, OutT* L, OutT* Y, unsigned char* defl,
+                         int* status, cudaStream_t st);
 template <typename T>
 void launch_syrk_sub(int s, int k, const T* C0, const T* SE, T* S, const int* status, cudaStream_t st);
 template <typename T>
