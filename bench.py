@@ -46,6 +46,8 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed node batches (0 = all after warm-up)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
+                    help="c2: graph node insertion (default, the headline); c4: 64 matrices, batched weight updates")
     ap.add_argument("--N", type=int, default=100_000)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--s", type=int, default=256)
@@ -166,10 +168,11 @@ def run_path(p, dev_batches, torch, dev, small, W, K, flush, profile=False, cloc
     ck = clocks.stop() if clocks else None
     ms = [a.elapsed_time(b) for a, b in evs[:len(pairs[W:W + K])]]
     code = h.status()
+    resets = h.small_state()[3]
     prof = h.profile_read() if profile else None
     U, s, V = h.get_factors(torch.float64)
     return dict(ms=ms, units=units, wall=wall, status=code, sigma=s.cpu().numpy(), launches=launches, clocks=ck,
-                profile=prof, handle=h, steps=len(ms))
+                profile=prof, handle=h, steps=len(ms), resets=int(resets))
 
 
 def run_e2e(p, batches, torch, dev, W, K):
@@ -296,10 +299,133 @@ def main_reference(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+C4_WORKLOAD = ("C4 batched weight updates A + D E^T: 64 independent matrices, m ~ U[5k, 200k], n = m/2, "
+               "k in {16,32,64,128}, s ~ U[8,128], 4 nnz per column of D and E; one step = one round of 64 updates")
+
+
+def c4_handles(p, torch, dev, small, jacobi_block, only_k=None):
+    """Handles for the C4 matrices with seeded random orthonormal starts made
+    on the device (the update step only sees the start factors)."""
+    from paper_2401_09703_gb300 import SVLCOV
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1004)
+    hs = []
+    for mat in p["mats"]:
+        if only_k is not None and mat["k"] != only_k:
+            continue
+        m, n, k = mat["m"], mat["n"], mat["k"]
+        U, _ = torch.linalg.qr(torch.randn(m, k, device=dev, generator=gen))
+        V, _ = torch.linalg.qr(torch.randn(n, k, device=dev, generator=gen))
+        sg = 10.0 * 0.97 ** torch.arange(k, device=dev, dtype=torch.float64)
+        max_s = max(b[0].rows for _, b in mat["batches"])
+        max_nnz = max(max(b[0].nnz, b[1].nnz) for _, b in mat["batches"])
+        hs.append(SVLCOV(U.contiguous(), sg, V.contiguous(), max_m=m, max_n=n, max_s=max_s, max_nnz=max_nnz,
+                         storage="fp32", small=small, jacobi_block=jacobi_block))
+        del U, V
+    return hs
+
+
+def main_c4(args):
+    import torch
+    from paper_2401_09703_gb300 import DeviceCSR, batch_run, kernel_launches
+    from paper_2401_09703_gb300 import autotune
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    p = synth.c4_problem(start="none")
+    R = len(p["mats"][0]["batches"])
+    W = max(1, min(args.warmup, R - 1))
+    K = args.steps if args.steps > 0 else R - W
+    K = max(1, min(K, R - W))
+    dbat = [[(DeviceCSR.from_host(D.indptr, D.indices, D.values, D.rows, D.cols, device=dev),
+              DeviceCSR.from_host(E.indptr, E.indices, E.values, E.rows, E.cols, device=dev))
+             for _, (D, E) in mat["batches"]] for mat in p["mats"]]
+    srows = [[b[0].rows for _, b in mat["batches"]] for mat in p["mats"]]
+
+    def items(hs, r, sel):
+        return [(h, "weights", dbat[i][r]) for h, i in zip(hs, sel)]
+
+    def run(small, conc, blk, graph, only_k=None):
+        sel = [i for i, mat in enumerate(p["mats"]) if only_k is None or mat["k"] == only_k]
+        hs = c4_handles(p, torch, dev, small, blk, only_k)
+        for r in range(W):
+            if conc == 0:
+                for h, i in zip(hs, sel):
+                    h.update_weights(*dbat[i][r])
+            else:
+                batch_run(items(hs, r, sel), conc)
+        torch.cuda.synchronize()
+        units = sum(srows[i][r] for i in sel for r in range(W, W + K))
+        s = torch.cuda.Stream()
+        g = None
+        note = None
+        if graph:
+            try:
+                g = torch.cuda.CUDAGraph()
+                with torch.cuda.stream(s):
+                    with torch.cuda.graph(g, stream=s):
+                        for r in range(W, W + K):
+                            batch_run(items(hs, r, sel), conc, stream=s)
+            except Exception as e:  # graph capture is an optimisation; report and run without it
+                note = f"graph capture failed: {type(e).__name__}"
+                g = None
+                torch.cuda.synchronize()
+                hs = c4_handles(p, torch, dev, small, blk, only_k)
+                for r in range(W):
+                    batch_run(items(hs, r, sel), conc)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = kernel_launches()
+        with torch.cuda.stream(s):
+            e0.record(s)
+            if g is not None:
+                g.replay()
+            else:
+                for r in range(W, W + K):
+                    if conc == 0:
+                        for h, i in zip(hs, sel):
+                            h.update_weights(*dbat[i][r], stream=s)
+                    else:
+                        batch_run(items(hs, r, sel), conc, stream=s)
+            e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        bad = sum(1 for h in hs if h.status() != 0)
+        resets = sum(h.small_state()[3] for h in hs)
+        del hs, g
+        torch.cuda.empty_cache()
+        return dict(value=units / (ms / 1e3), unit=UNIT, ms_per_step=ms / K, launches=kernel_launches() - l0,
+                    bad_status=bad, note=note, matrices=len(sel), resets_total=int(resets))
+
+    sig = "c4:" + ",".join(str(mat["k"]) for mat in p["mats"])
+
+    def make_handles(blk):
+        return c4_handles(p, torch, dev, "mixed", blk)
+
+    conc, blk, timings = autotune.tune(make_handles, lambda hs, r: items(hs, r, list(range(len(hs)))), sig,
+                                       cache_path=os.path.join(ROOT, "gpurun_out", "autotune_c4.json")
+                                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+    res = dict(mixed_graph=run("mixed", conc, blk, True), mixed_streams=run("mixed", conc, blk, False),
+               plain_sequential=run("fp32", 0, 16, False),
+               k64_mixed_graph=run("mixed", conc, blk, True, only_k=64),
+               k64_plain_sequential=run("fp32", 0, 16, False, only_k=64))
+    head = res["mixed_graph"]
+    line = dict(metric=METRIC, value=head["value"], unit=UNIT, n_gpus=1, steps=K, warmup=W,
+                ms_per_step=head["ms_per_step"], higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="f32 storage, f32+f64 small steps", data="synthetic",
+                config=dict(workload=C4_WORKLOAD, global_batch=None, l2="factors of all 64 matrices (~2.4 GB) exceed L2",
+                            autotuned=dict(concurrency=conc, jacobi_block=blk, timings_ms=timings)),
+                paths=res)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return main_reference(args)
+    if args.workload == "c4":
+        return main_c4(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:
@@ -361,7 +487,7 @@ def main():
             plain_fp32=None if plain is None else dict(value=plain["units"] / (sum(plain["ms"]) / 1e3), unit=UNIT,
                                                        ms_per_step=sum(plain["ms"]) / len(plain["ms"]),
                                                        sigma_rel_err_vs_oracle=err["plain"], status=plain["status"]),
-            sigma_rel_err_vs_oracle=err["mixed"], status=mixed["status"],
+            sigma_rel_err_vs_oracle=err["mixed"], status=mixed["status"], resets=mixed["resets"],
             roofline=roof, phases_ms=phases, e2e=e2e, cpu_baseline=cpu,
             gpu_launches=int(mixed["launches"]), clocks=mixed["clocks"],
             wall_s_timed_region=mixed["wall"])

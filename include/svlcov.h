@@ -102,7 +102,17 @@ typedef struct {
   size_t workspace_bytes; /*   256-byte aligned                                  */
   double tau;             /* deflation threshold (<= 0: default for `small`)     */
   double reset_threshold; /* cond_1 bound on U'', V'' (<= 0: default for storage) */
+  int32_t jacobi_block;   /* tile width of the Jacobi SVD: columns per block,   */
+                          /*   1..16 (<= 0: 16); a tuning knob, see autotune    */
 } svlcov_init_desc;
+
+/* One item of a batched run: kind 0 = add columns (a), 1 = add rows (a),
+ * 2 = update weights (a = D^T, b = E_m^T). */
+typedef struct {
+  int32_t kind;
+  svlcov_csr a;
+  svlcov_csr b;
+} svlcov_op;
 
 /* Size in bytes of the device workspace that `d` needs (host only, no CUDA
  * call).  Reads m, n, k, max_s, max_nnz, small; returns 0 on bad arguments. */
@@ -180,6 +190,18 @@ int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host
  * weight update.  Column-major; *rows, *cols receive the shape. */
 int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
                             size_t capacity_doubles, int32_t* rows, int32_t* cols, void* stream);
+
+/* Batched updates of many independent handles (configuration "many
+ * matrices, uneven k, s and nnz").  Items are enqueued in order on
+ * `concurrency` internal streams (1..64) forked from `stream` and joined back
+ * into it; all items of one handle go to the same internal stream, so they
+ * stay ordered, while different handles run concurrently.  Every handle
+ * needs its own workspace.  The call only enqueues work; it can be captured
+ * in a CUDA graph by capturing `stream`.  Each item is checked as by the
+ * single-item calls; on the first host error nothing more is enqueued, the
+ * streams are joined and the error is returned. */
+int svlcov_batch_run(svlcov_handle** handles, const svlcov_op* ops, int32_t n_ops, int32_t concurrency,
+                     void* stream);
 
 /* Phase timing (the only tracing the library does).  When enabled, every
  * step records CUDA events on its stream around six phases: 0 validation and

@@ -37,7 +37,11 @@ class svlcov_init_desc(C.Structure):
                 ("U0", C.c_void_p), ("sigma0", C.c_void_p), ("V0", C.c_void_p), ("init_dtype", C.c_int32),
                 ("ubuf", C.c_void_p), ("vbuf", C.c_void_p),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("tau", C.c_double), ("reset_threshold", C.c_double)]
+                ("tau", C.c_double), ("reset_threshold", C.c_double), ("jacobi_block", C.c_int32)]
+
+
+class svlcov_op(C.Structure):
+    _fields_ = [("kind", C.c_int32), ("a", svlcov_csr), ("b", svlcov_csr)]
 
 
 # name -> (restype, argtypes)
@@ -65,6 +69,7 @@ SIGNATURES = {
     "svlcov_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                       C.POINTER(C.c_int64)]),
     "svlcov_kernel_launches": (C.c_uint64, []),
+    "svlcov_batch_run": (C.c_int, [C.POINTER(C.c_void_p), C.POINTER(svlcov_op), C.c_int32, C.c_int32, C.c_void_p]),
     "svlcov_destroy": (None, [C.c_void_p]),
     "svlcov_strerror": (C.c_char_p, [C.c_int32]),
     "svlcov_small_svd_work_bytes": (C.c_size_t, [C.c_int32]),

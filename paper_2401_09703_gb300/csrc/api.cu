@@ -4,7 +4,9 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <mutex>
 #include <new>
+#include <unordered_map>
 #include <vector>
 
 #include "kernels.cuh"
@@ -180,6 +182,7 @@ static bool desc_ok(const svlcov_init_desc* d) {
   if (d->max_s < 1 || d->max_s > SVLCOV_MAX_S) return false;
   if (d->m < 0 || d->n < 0 || d->max_m < d->m || d->max_n < d->n || d->max_nnz < 0) return false;
   if (d->storage < SVLCOV_FP64 || d->storage > SVLCOV_BF16) return false;
+  if (d->jacobi_block > 16) return false;
   if (d->small < SVLCOV_SMALL_FP64 || d->small > SVLCOV_SMALL_MIXED) return false;
   return true;
 }
@@ -377,8 +380,8 @@ template <typename TC>
 static int small_svd_step(svlcov_handle* h, const TC* K, int n2, TC* F, TC* theta, TC* G, cudaStream_t st) {
   if (h->d.small == SVLCOV_SMALL_MIXED)
     return launch_mixed_svd((const double*)K, n2, h->k, (double*)F, (double*)theta, (double*)G, h->jwork, h->rwork,
-                            h->status, st, h->stats);
-  return launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats);
+                            h->status, st, h->stats, h->d.jacobi_block);
+  return launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats, h->d.jacobi_block);
 }
 
 template <typename TS, typename TC>
@@ -534,6 +537,68 @@ extern "C" int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, co
   if (rc == SVLCOV_OK) {
     h->last_op = 2;
     h->last_s = D_T->rows;
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Batched runs: a per-device pool of non-blocking streams and events.
+namespace {
+struct StreamPool {
+  std::vector<cudaStream_t> streams;
+  std::vector<cudaEvent_t> done;
+  cudaEvent_t fork = nullptr;
+};
+std::mutex g_pool_mu;
+std::unordered_map<int, StreamPool> g_pools;
+
+int pool_for(int need, StreamPool** out) {
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return SVLCOV_ERR_CUDA;
+  std::lock_guard<std::mutex> lock(g_pool_mu);
+  StreamPool& p = g_pools[dev];
+  if (!p.fork && cudaEventCreateWithFlags(&p.fork, cudaEventDisableTiming) != cudaSuccess) return SVLCOV_ERR_CUDA;
+  while ((int)p.streams.size() < need) {
+    cudaStream_t s;
+    cudaEvent_t e;
+    if (cudaStreamCreateWithFlags(&s, cudaStreamNonBlocking) != cudaSuccess) return SVLCOV_ERR_CUDA;
+    if (cudaEventCreateWithFlags(&e, cudaEventDisableTiming) != cudaSuccess) return SVLCOV_ERR_CUDA;
+    p.streams.push_back(s);
+    p.done.push_back(e);
+  }
+  *out = &p;
+  return SVLCOV_OK;
+}
+}  // namespace
+
+extern "C" int svlcov_batch_run(svlcov_handle** hs, const svlcov_op* ops, int32_t n_ops, int32_t concurrency,
+                                void* stream) {
+  if (!hs || (!ops && n_ops > 0) || n_ops < 0) return SVLCOV_ERR_INVALID_ARG;
+  if (n_ops == 0) return SVLCOV_OK;
+  int P = std::max(1, std::min(64, (int)concurrency));
+  StreamPool* pool = nullptr;
+  int rc = pool_for(P, &pool);
+  if (rc) return rc;
+  cudaStream_t st = (cudaStream_t)stream;
+  CUDA_OK(cudaEventRecord(pool->fork, st));
+  for (int i = 0; i < P; ++i) CUDA_OK(cudaStreamWaitEvent(pool->streams[i], pool->fork, 0));
+  std::unordered_map<svlcov_handle*, int> lane;  // handle -> its stream
+  int next = 0;
+  for (int32_t i = 0; i < n_ops && rc == SVLCOV_OK; ++i) {
+    svlcov_handle* h = hs[i];
+    if (!h) { rc = SVLCOV_ERR_INVALID_ARG; break; }
+    auto it = lane.find(h);
+    int li = it != lane.end() ? it->second : (lane[h] = next++ % P);
+    void* s2 = (void*)pool->streams[li];
+    const svlcov_op& op = ops[i];
+    if (op.kind == 0) rc = svlcov_add_cols(h, &op.a, s2);
+    else if (op.kind == 1) rc = svlcov_add_rows(h, &op.a, s2);
+    else if (op.kind == 2) rc = svlcov_update_weights(h, &op.a, &op.b, s2);
+    else rc = SVLCOV_ERR_INVALID_ARG;
+  }
+  for (int i = 0; i < P; ++i) {  // join, also after an error
+    CUDA_OK(cudaEventRecord(pool->done[i], pool->streams[i]));
+    CUDA_OK(cudaStreamWaitEvent(st, pool->done[i], 0));
   }
   return rc;
 }

@@ -83,10 +83,10 @@ size_t jacobi_work_bytes(int n);
 int* jacobi_sweeps_ptr(void* work, int n, int elem);
 size_t refine_work_bytes(int n, int k);
 int launch_mixed_svd(const double* K, int n, int k, double* F, double* theta, double* G, void* jwork, void* rwork,
-                     int* status, cudaStream_t st, int64_t* sweep_total);
+                     int* status, cudaStream_t st, int64_t* sweep_total, int bcap = 0);
 template <typename T>
 int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st,
-                  int64_t* sweep_total = nullptr);
+                  int64_t* sweep_total = nullptr, int bcap = 0);
 template <typename T>
 void launch_inverse(const T* W, int k, T* Winv, double thr, int* do_reset, int* status, cudaStream_t st);
 template <typename T>

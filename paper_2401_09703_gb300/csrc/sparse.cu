@@ -424,7 +424,12 @@ __global__ void k_rowmul(const TS* __restrict__ Xp, int64_t rows, int k, const T
   if (do_reset && *(volatile const int*)do_reset == 0) return;
   if (status && failed(status)) return;
   int nw = blockDim.x >> 5, wib = threadIdx.x >> 5, lane = threadIdx.x & 31;
-  for (int t = threadIdx.x; t < k * k; t += blockDim.x) wsm[t] = (A)W[t];
+  // W row-major in shared memory (wsm[b * k + a] = W(b, a)): lanes, which
+  // own consecutive output columns a, then read consecutive words
+  for (int t = threadIdx.x; t < k * k; t += blockDim.x) {
+    int b2 = t / k, a = t - b2 * k;
+    wsm[t] = (A)W[(int64_t)a * k + b2];
+  }
   A* xrow = wsm + k * k + wib * kMaxK;
   __syncthreads();
   for (int64_t r = (int64_t)blockIdx.x * nw + wib; r < rows; r += (int64_t)gridDim.x * nw) {
@@ -441,8 +446,7 @@ __global__ void k_rowmul(const TS* __restrict__ Xp, int64_t rows, int k, const T
     __syncwarp();
     for (int a = lane; a < k; a += 32) {
       A sum = (A)0;
-      const A* wa = wsm + (int64_t)a * k;
-      for (int b2 = 0; b2 < k; ++b2) sum = fma(xrow[b2], wa[b2], sum);
+      for (int b2 = 0; b2 < k; ++b2) sum = fma(xrow[b2], wsm[(int64_t)b2 * k + a], sum);
       out[r * k + a] = from_f64<TO>((double)sum);
     }
     __syncwarp();

@@ -64,7 +64,7 @@ class SVLCOV:
 
     def __init__(self, U0: torch.Tensor, sigma0: torch.Tensor, V0: torch.Tensor, *, max_m: int, max_n: int,
                  max_s: int, max_nnz: int, storage: str = "fp32", small: str = "mixed", tau: float = 0.0,
-                 reset_threshold: float = 0.0, stream=None):
+                 reset_threshold: float = 0.0, jacobi_block: int = 0, stream=None):
         assert U0.is_cuda and V0.is_cuda and sigma0.is_cuda
         m, k = U0.shape
         n = V0.shape[0]
@@ -85,6 +85,7 @@ class SVLCOV:
         d.U0, d.sigma0, d.V0, d.init_dtype = self._U0.data_ptr(), self._s0.data_ptr(), self._V0.data_ptr(), init_dtype
         d.ubuf, d.vbuf = self.ubuf.data_ptr(), self.vbuf.data_ptr()
         d.tau, d.reset_threshold = tau, reset_threshold
+        d.jacobi_block = jacobi_block
         nbytes = lib().svlcov_workspace_bytes(C.byref(d))
         if nbytes == 0:
             raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_workspace_bytes")
@@ -194,6 +195,27 @@ class SVLCOV:
         check(lib().svlcov_get_intermediate(self.h, which, side, out.ctypes.data_as(C.c_void_p), out.size,
                                             C.byref(r), C.byref(c), _stream(stream)), "svlcov_get_intermediate")
         return out.reshape(c.value, r.value).T   # column-major on the device
+
+
+_KIND = {"cols": 0, "rows": 1, "weights": 2}
+
+
+def batch_run(items, concurrency: int = 16, stream=None):
+    """Enqueue many (handle, op, batch) items: svlcov_batch_run.  `items` is
+    a list of (SVLCOV, "cols"|"rows"|"weights", DeviceCSR or (D, E))."""
+    n = len(items)
+    hs = (C.c_void_p * n)()
+    ops = (_abi.svlcov_op * n)()
+    for i, (h, op, batch) in enumerate(items):
+        hs[i] = h.h
+        ops[i].kind = _KIND[op]
+        if op == "weights":
+            ops[i].a = batch[0].c()
+            ops[i].b = batch[1].c()
+        else:
+            ops[i].a = batch.c()
+    check(lib().svlcov_batch_run(hs, ops, n, int(concurrency), _stream(stream)), "svlcov_batch_run")
+    # the host view of each handle's shape follows the enqueued appends
 
 
 def kernel_launches() -> int:

@@ -253,32 +253,64 @@ def c3_problem(seed: int = 1003, n_users: int = 1_000_000, n_items: int = 50_000
 # --------------------------------------------------------------------------
 def random_csr_batch(s: int, d: int, per_vec: int, g: np.random.Generator) -> CSR:
     """``s`` update vectors of length ``d``, each with ``per_vec`` distinct
-    uniform positions holding N(0,1) values."""
-    r, c = [], []
-    for j in range(s):
-        pos = g.choice(d, size=min(per_vec, d), replace=False)
-        r.extend([j] * pos.shape[0])
-        c.extend(pos.tolist())
-    return csr_from_coo(np.array(r, dtype=np.int64), np.array(c, dtype=np.int64),
-                        g.standard_normal(len(r)), s, d, shuffle_within_rows=g)
+    uniform positions holding N(0,1) values (duplicates within a vector are
+    redrawn)."""
+    p = min(per_vec, d)
+    pos = g.integers(0, d, size=(s, p))
+    for _ in range(1000):
+        srt = np.sort(pos, axis=1)
+        dup = np.zeros_like(pos, dtype=bool)
+        if p > 1:
+            dup_rows = np.any(srt[:, 1:] == srt[:, :-1], axis=1)
+        else:
+            dup_rows = np.zeros(s, dtype=bool)
+        if not dup_rows.any():
+            break
+        pos[dup_rows] = g.integers(0, d, size=(int(dup_rows.sum()), p))
+    r = np.repeat(np.arange(s, dtype=np.int64), p)
+    return csr_from_coo(r, pos.reshape(-1).astype(np.int64), g.standard_normal(s * p), s, d,
+                        shuffle_within_rows=g)
+
+
+def random_start(m: int, n: int, k: int, g: np.random.Generator, decay: float = 0.97):
+    """A seeded orthonormal rank-k start (Gaussian QR) with geometrically
+    decaying singular values: a valid start of the update step that does not
+    need the matrix it came from."""
+    U, _ = np.linalg.qr(g.standard_normal((m, k), dtype=np.float32).astype(np.float64))
+    V, _ = np.linalg.qr(g.standard_normal((n, k), dtype=np.float32).astype(np.float64))
+    sig = 10.0 * decay ** np.arange(k)
+    return U, sig, V
 
 
 def c4_problem(seed: int = 1004, n_mats: int = 64, m_lo: int = 5_000, m_hi: int = 200_000,
                density: float = 1e-4, ks=(16, 32, 64, 128), n_batches: int = 10,
-               s_lo: int = 8, s_hi: int = 128, per_vec: int = 4, power_iters: int = 2) -> dict:
+               s_lo: int = 8, s_hi: int = 128, per_vec: int = 4, power_iters: int = 2,
+               start: str = "rsvd") -> dict:
     """Independent Gaussian sparse matrices (m ~ U[m_lo, m_hi], n = m // 2,
     density 1e-4), each with ``n_batches`` weight updates D E^T of a random
-    width s ~ U[s_lo, s_hi] and ``per_vec`` nonzeros per column of D and E."""
+    width s ~ U[s_lo, s_hi] and ``per_vec`` nonzeros per column of D and E.
+
+    start="rsvd": the start is a randomized SVD of the drawn matrix A.
+    start="random": A is not drawn; the start is ``random_start`` (the update
+    step only ever sees the start factors and the batches, so its work is the
+    same; used for benchmark-size runs where drawing A dominates).
+    start="none": A and the start are left to the caller (U, sigma, V None)."""
     g = rng(seed)
     mats = []
     for _ in range(n_mats):
         m = int(g.integers(m_lo, m_hi + 1))
         n = m // 2
         k = int(g.choice(np.array(ks)))
-        nnz = max(1, int(round(density * m * n)))
-        flat = np.unique(g.integers(0, m * n, size=nnz))
-        A = sp.csr_matrix((g.standard_normal(flat.shape[0]), (flat // n, flat % n)), shape=(m, n))
-        U, sig, V = init_factors(A, k, int(g.integers(1 << 30)), power_iters=power_iters)
+        if start == "none":
+            A, U, sig, V = None, None, None, None
+        elif start == "random":
+            A = None
+            U, sig, V = random_start(m, n, k, g)
+        else:
+            nnz = max(1, int(round(density * m * n)))
+            flat = np.unique(g.integers(0, m * n, size=nnz))
+            A = sp.csr_matrix((g.standard_normal(flat.shape[0]), (flat // n, flat % n)), shape=(m, n))
+            U, sig, V = init_factors(A, k, int(g.integers(1 << 30)), power_iters=power_iters)
         batches = []
         for _ in range(n_batches):
             s = int(g.integers(s_lo, s_hi + 1))
