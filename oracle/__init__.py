@@ -15,6 +15,8 @@ Three independent FP64 implementations of one update step:
   SV-LCOV space) with Algorithms 3, 4 and 11 acting on the extended
   decomposition U' U'' Sigma V''^T V'^T of Section 3.2.
 
-``checks`` holds the error measures used to compare results.
+``checks`` holds the error measures used to compare results; ``backward``
+the reference gradient of one add-columns step (torch float64 autograd of
+the dense formulation, and finite differences of the sparse method).
 """
 from . import dense, svlcov, checks  # noqa: F401

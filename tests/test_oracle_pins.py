@@ -375,3 +375,43 @@ def test_planted_mistakes_are_caught(variant, monkeypatch):
     err = max(checks.sigma_rel_err(ss, sd), checks.projector_err(Us, Ud), checks.projector_err(Vs, Vd),
               checks.orth_err(Us), checks.orth_err(Vs))
     assert err > 1e-6, (variant, err)
+
+
+# ---------------------------------------------------------------------------
+def nonempty_columns(b):
+    """The batch without its empty update vectors (the gradient of a
+    deflated direction does not exist; the differentiation workload uses
+    batches with none, reading R14)."""
+    keep = [j for j in range(b.rows) if b.indptr[j + 1] > b.indptr[j]]
+    r, c, v = [], [], []
+    for jj, j in enumerate(keep):
+        a, e = b.indptr[j], b.indptr[j + 1]
+        r.extend([jj] * (e - a)); c.extend(b.indices[a:e].tolist()); v.extend(b.values[a:e].tolist())
+    return synth.csr_from_coo(np.array(r, dtype=np.int64), np.array(c, dtype=np.int64), np.array(v), len(keep), b.cols)
+
+
+def _c5_small(seed=51, N=1200, k=8, s=12):
+    p = synth.c2_problem(seed=seed, N=N, k=k, s=s, n_batches=2, power_iters=2)
+    kind, b = p["batches"][1]          # a column step
+    assert kind == "cols"
+    b = nonempty_columns(b)
+    st = svlcov.State.init(p["U"], p["sigma"], p["V"])
+    st.apply(*p["batches"][0])         # the row step before it
+    U, sg, V = st.factors()
+    g = synth.rng(seed)
+    S_rows = np.sort(g.choice(U.shape[0], size=200, replace=False))
+    return U, sg, V, b, S_rows
+
+
+def test_gradient_autograd_matches_finite_differences():
+    """The reference gradient of the C5 loss (torch float64 autograd on the
+    dense Zha-Simon step) equals central finite differences of the sparse
+    oracle's loss (h = 1e-3) on random nonzeros, to 1e-5 normwise."""
+    from oracle import backward
+    U, sg, V, b, S_rows = _c5_small()
+    ga = backward.grad_autograd(U, sg, b.indptr, b.indices, b.values, b.rows, S_rows)
+    g = synth.rng(3)
+    which = g.choice(b.nnz, size=min(16, b.nnz), replace=False)
+    gf = backward.grad_fd(U, sg, V, b.indptr, b.indices, b.values, b.rows, S_rows, which)
+    assert np.linalg.norm(ga[which] - gf) <= 1e-5 * np.linalg.norm(gf)
+    assert np.linalg.norm(gf) > 0
