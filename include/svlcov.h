@@ -49,7 +49,7 @@ extern "C" {
 #define SVLCOV_ERR_INVALID_ARG 1 /* host: null pointer, bad shape, unsupported k or s */
 #define SVLCOV_ERR_CAPACITY 2    /* host: would exceed max_m/max_n/max_s/max_nnz or the workspace */
 #define SVLCOV_ERR_CUDA 3        /* host: a CUDA runtime call failed */
-#define SVLCOV_ERR_STATE 4       /* host: a device error is pending; call svlcov_status first */
+#define SVLCOV_ERR_STATE 4       /* host: the handle is not in the state the call needs */
 /* device status bits (OR-ed), reported by svlcov_status */
 #define SVLCOV_DEV_BAD_CSR 0x10   /* indptr not monotone/out of range, index out of range, duplicate */
 #define SVLCOV_DEV_NONFINITE 0x20 /* NaN/Inf in batch values or in a small-step result */
@@ -190,6 +190,39 @@ int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host
  * weight update.  Column-major; *rows, *cols receive the shape. */
 int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
                             size_t capacity_doubles, int32_t* rows, int32_t* cols, void* stream);
+
+/* Backward of the last add-columns step (Algorithm 3; the fold of Section
+ * 3.2): the gradient of a loss L(U_new[S], Theta) with respect to the stored
+ * values of that step's batch E_c, from the intermediates the step left in
+ * the workspace.  Valid only right after svlcov_add_cols on this handle (no
+ * other call in between, ERR_STATE otherwise), with small mode FP64 or MIXED
+ * (ERR_INVALID_ARG otherwise), for a batch with no empty or dependent update
+ * vector (a deflated direction has no gradient).  The gradient is that of
+ * the exact update, which does not depend on how the step stored its
+ * factors.  All pointers device, FP64, row-major:
+ *   E          the batch as passed to svlcov_add_cols
+ *   rows_S     nS rows of U, strictly ascending (0 <= nS <= m)
+ *   U_pre_S    nS x k, rows rows_S of the left factor BEFORE the step
+ *   U_pre_nnz  nnz x k, the left-factor row (before the step) of each
+ *              nonzero of E, in CSR order
+ *   dL_dU_S    nS x k, dL/dU_new at rows rows_S
+ *   dL_dtheta  k, dL/dTheta (may be NULL for zero)
+ *   dL_dvalues nnz output, dL/de for each nonzero, in CSR order
+ * gap: singular-value pairs (one of them kept) closer than gap * theta_1
+ * are left out of the SVD adjoint, whose pair coefficient is
+ * 1 / (theta_j^2 - theta_i^2), and raise SVLCOV_DEV_GAP_WARN in the status
+ * word (<= 0 picks 1e-6; the leading singular values of sparse power-law
+ * matrices lie ~1e-4 * theta_1 apart, and their pair terms are part of the
+ * gradient).  work: device scratch of svlcov_add_cols_backward_work_bytes(h)
+ * bytes.  Asynchronous on `stream`; the full SVD of K it needs runs in the
+ * handle's small precision (FP64 sweeps, or FP32 sweeps + FP64 refinement).
+ * Device-side problems set status bits as for a step; svlcov_set_state
+ * invalidates the step's intermediates. */
+size_t svlcov_add_cols_backward_work_bytes(const svlcov_handle* h);
+int svlcov_add_cols_backward(svlcov_handle* h, const svlcov_csr* E, const int32_t* rows_S, int32_t nS,
+                             const double* U_pre_S, const double* U_pre_nnz, const double* dL_dU_S,
+                             const double* dL_dtheta, double* dL_dvalues, double gap, void* work,
+                             void* stream);
 
 /* Batched updates of many independent handles (configuration "many
  * matrices, uneven k, s and nnz").  Items are enqueued in order on

@@ -65,6 +65,10 @@ SIGNATURES = {
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "svlcov_get_intermediate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
+    "svlcov_add_cols_backward_work_bytes": (C.c_size_t, [C.c_void_p]),
+    "svlcov_add_cols_backward": (C.c_int, [C.c_void_p, C.POINTER(svlcov_csr), C.c_void_p, C.c_int32, C.c_void_p,
+                                           C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,
+                                           C.c_void_p]),
     "svlcov_profile_enable": (C.c_int, [C.c_void_p, C.c_int32]),
     "svlcov_profile_read": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_int32,
                                       C.POINTER(C.c_int64)]),

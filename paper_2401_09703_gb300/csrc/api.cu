@@ -756,6 +756,7 @@ extern "C" int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const vo
   CUDA_OK(cudaMemset(h->status, 0, sizeof(int)));
   h->m = m;
   h->n = n;
+  h->last_op = -1;  // the step intermediates no longer belong to this state
   return SVLCOV_OK;
 }
 
@@ -785,13 +786,42 @@ extern "C" int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t 
   return copy_small_to_host(h, src, host_out, (int64_t)r * c);
 }
 
+// ---------------------------------------------------------------------------
+// Backward of the last add-columns step (FP64 small state).
+extern "C" size_t svlcov_add_cols_backward_work_bytes(const svlcov_handle* h) {
+  if (!h) return 0;
+  int s = (int)h->d.max_s;
+  return backward_work_bytes(h->k + s, h->k, s, std::max<int64_t>(h->d.max_nnz, 1));
+}
+
+extern "C" int svlcov_add_cols_backward(svlcov_handle* h, const svlcov_csr* E, const int32_t* rows_S, int32_t nS,
+                                        const double* U_pre_S, const double* U_pre_nnz, const double* dL_dU_S,
+                                        const double* dL_dtheta, double* dL_dvalues, double gap, void* work,
+                                        void* stream) {
+  if (!h || !csr_ok(E) || !work) return SVLCOV_ERR_INVALID_ARG;
+  if (h->d.small != SVLCOV_SMALL_FP64 && h->d.small != SVLCOV_SMALL_MIXED) return SVLCOV_ERR_INVALID_ARG;
+  if (h->last_op != 0 || E->rows != h->last_s) return SVLCOV_ERR_STATE;
+  if (nS < 0 || nS > h->m || (nS > 0 && (!rows_S || !U_pre_S || !dL_dU_S))) return SVLCOV_ERR_INVALID_ARG;
+  if (E->nnz > 0 && (!U_pre_nnz || !dL_dvalues)) return SVLCOV_ERR_INVALID_ARG;
+  const SideBufs& sb = h->side[0];
+  BackwardInputs in{};
+  in.C0 = sb.C0; in.R = sb.R; in.X = sb.X; in.CQ = sb.CQ; in.Y = sb.Y;
+  in.K = h->K; in.F = h->F; in.G = h->G; in.theta = h->theta;
+  in.rowid = sb.sc.rowid; in.slot = sb.sc.slot; in.hstart = sb.sc.hstart; in.hcnt = sb.sc.hcnt;
+  in.seg_j = sb.sc.seg_j; in.seg_v = sb.sc.seg_v;
+  in.jwork = h->jwork;
+  in.mixed = h->d.small == SVLCOV_SMALL_MIXED;
+  return launch_add_cols_backward(*E, h->k, in, rows_S, nS, U_pre_S, U_pre_nnz, dL_dU_S, dL_dtheta, dL_dvalues,
+                                  gap > 0 ? gap : 1e-6, work, h->status, (cudaStream_t)stream);
+}
+
 extern "C" const char* svlcov_strerror(int32_t code) {
   switch (code) {
     case SVLCOV_OK: return "ok";
     case SVLCOV_ERR_INVALID_ARG: return "invalid argument";
     case SVLCOV_ERR_CAPACITY: return "capacity exceeded";
     case SVLCOV_ERR_CUDA: return "CUDA runtime error";
-    case SVLCOV_ERR_STATE: return "device error pending";
+    case SVLCOV_ERR_STATE: return "handle not in the state the call needs";
     case SVLCOV_DEV_BAD_CSR: return "malformed CSR batch";
     case SVLCOV_DEV_NONFINITE: return "non-finite value";
     case SVLCOV_DEV_NOT_PD: return "residual Gram matrix not finite";

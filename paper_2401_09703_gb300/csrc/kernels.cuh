@@ -111,4 +111,20 @@ template <typename T> struct FiniteSet {
 template <typename T>
 void launch_check_finite_multi(const FiniteSet<T>& set, int* status, cudaStream_t st);
 
+// ---- backward of one add-columns step (FP64 small state) -------------------
+// Intermediates the forward step left in the workspace (column-major, FP64).
+struct BackwardInputs {
+  const double *C0, *R, *X, *CQ, *Y;        // k x s, s x s, s x s, k x s, s x k
+  const double *K, *F, *G, *theta;          // (k+s)^2, (k+s) x k, (k+s) x k, k
+  const int *rowid, *slot, *hstart, *hcnt;  // CSR row of each nonzero; grouped view
+  const int* seg_j;
+  const double* seg_v;
+  void* jwork;                              // Jacobi scratch for k + s
+  bool mixed;                               // full SVD of K: FP32 sweeps + FP64 refinement, else FP64 sweeps
+};
+size_t backward_work_bytes(int n, int k, int s, int64_t nnz);
+int launch_add_cols_backward(const svlcov_csr& E, int k, const BackwardInputs& in, const int32_t* S, int nS,
+                             const double* Upre_S, const double* Upre_nnz, const double* Ubar, const double* thbar,
+                             double* dvalues, double gap, void* work, int* status, cudaStream_t st);
+
 }  // namespace svl

@@ -146,6 +146,33 @@ class SVLCOV:
               "svlcov_query_rows")
         return out
 
+    def sigma(self, stream=None) -> torch.Tensor:
+        """The current singular values (device, FP64)."""
+        s = torch.empty(self.k, dtype=torch.float64, device=self.device)
+        check(lib().svlcov_get_factors(self.h, None, _ptr(s), None, _abi.SVLCOV_FP64, _stream(stream)),
+              "svlcov_get_factors")
+        return s
+
+    def add_cols_backward(self, batch: DeviceCSR, rows_S: torch.Tensor, U_pre_S: torch.Tensor,
+                          U_pre_nnz: torch.Tensor, dU_S: torch.Tensor, dtheta: Optional[torch.Tensor],
+                          gap: float = 1e-6, stream=None) -> torch.Tensor:
+        """dL/d(batch values) of the last add_cols step (svlcov_add_cols_backward)."""
+        dev = self.device
+        rows_S = rows_S.to(device=dev, dtype=torch.int32).contiguous()
+        f64 = lambda t: t.to(device=dev, dtype=torch.float64).contiguous()
+        U_pre_S, U_pre_nnz, dU_S = f64(U_pre_S), f64(U_pre_nnz), f64(dU_S)
+        dtheta = None if dtheta is None else f64(dtheta)
+        out = torch.empty(batch.nnz, dtype=torch.float64, device=dev)
+        nb = lib().svlcov_add_cols_backward_work_bytes(self.h)
+        if getattr(self, "_bw_work", None) is None or self._bw_work.numel() < nb + 256:
+            self._bw_work = torch.empty(nb + 256, dtype=torch.uint8, device=dev)
+        wp = (self._bw_work.data_ptr() + 255) & ~255
+        check(lib().svlcov_add_cols_backward(self.h, C.byref(batch.c()), _ptr(rows_S), rows_S.numel(),
+                                             _ptr(U_pre_S), _ptr(U_pre_nnz), _ptr(dU_S), _ptr(dtheta), _ptr(out),
+                                             float(gap), C.c_void_p(wp), _stream(stream)),
+              "svlcov_add_cols_backward")
+        return out
+
     def status(self, stream=None) -> int:
         code = C.c_int32()
         check(lib().svlcov_status(self.h, C.byref(code), _stream(stream)), "svlcov_status")
@@ -195,6 +222,39 @@ class SVLCOV:
         check(lib().svlcov_get_intermediate(self.h, which, side, out.ctypes.data_as(C.c_void_p), out.size,
                                             C.byref(r), C.byref(c), _stream(stream)), "svlcov_get_intermediate")
         return out.reshape(c.value, r.value).T   # column-major on the device
+
+
+class _AddColsGrad(torch.autograd.Function):
+    """One add-columns step as a differentiable function of the batch's
+    stored values: returns (U_new[rows_S], Theta).  The backward runs the
+    library's adjoint kernels and must come before the next step on the
+    same handle (its intermediates live in the handle's workspace)."""
+
+    @staticmethod
+    def forward(ctx, values, model, batch, rows_S, gap):
+        b = DeviceCSR(batch.indptr, batch.indices, values.detach(), batch.rows, batch.cols)
+        U_pre_S = model.query_rows(0, rows_S)
+        U_pre_nnz = model.query_rows(0, batch.indices)
+        model.add_cols(b)
+        ctx.model, ctx.batch, ctx.gap, ctx.vdtype = model, b, gap, values.dtype
+        ctx.save_for_backward(rows_S, U_pre_S, U_pre_nnz)
+        return model.query_rows(0, rows_S), model.sigma()
+
+    @staticmethod
+    def backward(ctx, dU_S, dtheta):
+        rows_S, U_pre_S, U_pre_nnz = ctx.saved_tensors
+        g = ctx.model.add_cols_backward(ctx.batch, rows_S, U_pre_S, U_pre_nnz, dU_S, dtheta, ctx.gap)
+        return g.to(ctx.vdtype), None, None, None, None
+
+
+def add_cols_with_grad(model: SVLCOV, batch: DeviceCSR, rows_S: torch.Tensor, gap: float = 1e-6):
+    """model.add_cols(batch), differentiable in batch.values: returns
+    (U_new[rows_S] (FP64), Theta (FP64)).  rows_S: existing rows of U, strictly
+    ascending.  Needs small mode "fp64" or "mixed" and a batch without empty
+    update vectors; after backward, model.status() reports SVLCOV_DEV_GAP_WARN
+    if a singular-value pair fell under the gap guard."""
+    rows_S = rows_S.to(device=model.device, dtype=torch.int32).contiguous()
+    return _AddColsGrad.apply(batch.values, model, batch, rows_S, gap)
 
 
 _KIND = {"cols": 0, "rows": 1, "weights": 2}

@@ -6,6 +6,6 @@ input of every update step) from fixed seeds.
 """
 from .generators import (  # noqa: F401
     CSR, csr_from_coo, csr_to_scipy, rng,
-    c1_problem, c2_problem, c3_problem, c4_problem,
+    c1_problem, c2_problem, c3_problem, c4_problem, c5_problem, distinct_nonempty_rows,
     chung_lu_edges, init_factors, random_csr_batch, random_start,
 )

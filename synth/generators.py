@@ -198,6 +198,49 @@ def c2_problem(seed: int = 1002, N: int = 100_000, gamma: float = 2.1, mean_deg:
 
 
 # --------------------------------------------------------------------------
+# C5: one differentiated column step of C2
+# --------------------------------------------------------------------------
+def distinct_nonempty_rows(b: CSR) -> CSR:
+    """The batch without its empty update vectors and without repeats of an
+    earlier vector (same indices and values).  Such vectors are dependent, and
+    the differentiated step needs independent ones."""
+    seen, keep = set(), []
+    for j in range(b.rows):
+        a, e = int(b.indptr[j]), int(b.indptr[j + 1])
+        if e == a:
+            continue
+        key = tuple(sorted(zip(b.indices[a:e].tolist(), b.values[a:e].tolist())))
+        if key in seen:
+            continue
+        seen.add(key)
+        keep.append(j)
+    r, c, v = [], [], []
+    for jj, j in enumerate(keep):
+        a, e = int(b.indptr[j]), int(b.indptr[j + 1])
+        r.extend([jj] * (e - a))
+        c.extend(b.indices[a:e].tolist())
+        v.extend(b.values[a:e].tolist())
+    return csr_from_coo(np.asarray(r, dtype=np.int64), np.asarray(c, dtype=np.int64), np.asarray(v, dtype=np.float64),
+                        len(keep), b.cols)
+
+
+def c5_problem(seed: int = 1002, N: int = 100_000, k: int = 64, s: int = 256, n_loss: int = 4096,
+               loss_seed: int = 1005, power_iters: int = 4) -> dict:
+    """C2's start, its first node batch, and the loss rows of the
+    differentiation workload: the row step runs first (the caller applies
+    it), then the column step ``cols`` (the first column batch, restricted to
+    its distinct non-empty update vectors) is differentiated for the loss over
+    ``n_loss`` seeded random existing rows ``S_rows`` (sorted)."""
+    p = c2_problem(seed=seed, N=N, k=k, s=s, n_batches=1, power_iters=power_iters)
+    (kr, rows), (kc, cols) = p["batches"][0], p["batches"][1]
+    assert kr == "rows" and kc == "cols"
+    g = rng(loss_seed)
+    S_rows = np.sort(g.choice(p["n0"], size=min(n_loss, p["n0"]), replace=False)).astype(np.int64)
+    return dict(name="C5", U=p["U"], sigma=p["sigma"], V=p["V"], k=k, rows=rows,
+                cols=distinct_nonempty_rows(cols), cols_raw=cols, S_rows=S_rows, N=N)
+
+
+# --------------------------------------------------------------------------
 # C3: rating matrix, users appended as rows
 # --------------------------------------------------------------------------
 def zipf_ratings(n_users: int, n_items: int, mean_per_user: float, zipf_a: float,
