@@ -46,8 +46,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed node batches (0 = all after warm-up)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4"],
-                    help="c2: graph node insertion (default, the headline); c4: 64 matrices, batched weight updates")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
+                    help="c2: graph node insertion (default, the headline); c4: 64 matrices, batched weight updates; "
+                         "c5: forward + backward of one differentiated column step")
     ap.add_argument("--N", type=int, default=100_000)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--s", type=int, default=256)
@@ -420,12 +421,104 @@ def main_c4(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+C5_WORKLOAD = ("C5 differentiated column step: C2's first node batch (Chung-Lu N=100000, k=64; the add_rows step "
+               "first, untimed), then add_cols with its distinct non-empty update vectors (194 of s=256) "
+               "differentiated for L = sum over 4096 existing nodes of ||U_new[r] Theta^1/2||^2; "
+               "one step = forward + backward (torch autograd through the library's adjoint)")
+
+
+def main_c5(args):
+    import torch
+    from paper_2401_09703_gb300 import SVLCOV, DeviceCSR, add_cols_with_grad, kernel_launches
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    p = synth.c5_problem()
+    b, S_rows = p["cols"], p["S_rows"]
+    N = p["N"]
+
+    def to_dev(x, dtype):
+        return DeviceCSR.from_host(x.indptr, x.indices, x.values, x.rows, x.cols, device=dev, values_dtype=dtype)
+
+    def run(storage, small, W, K):
+        idt = torch.float64 if storage == "fp64" else torch.float32
+        h = SVLCOV(torch.as_tensor(p["U"], dtype=idt, device=dev),
+                   torch.as_tensor(p["sigma"], device=dev), torch.as_tensor(p["V"], dtype=idt, device=dev),
+                   max_m=N + 64, max_n=N + 64, max_s=max(b.rows, p["rows"].rows),
+                   max_nnz=max(b.nnz, p["rows"].nnz), storage=storage, small=small)
+        h.add_rows(to_dev(p["rows"], torch.float32))
+        state = h.get_state()
+        S = torch.as_tensor(S_rows, dtype=torch.int32, device=dev)
+        batch = to_dev(b, torch.float64)
+        flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+        stream = torch.cuda.current_stream()
+        fwd, bwd, grads = [], [], None
+        l0 = None
+        for it in range(W + K):
+            h.set_state(state)
+            flush.zero_()
+            v = batch.values.detach().clone().requires_grad_(True)
+            bt = DeviceCSR(batch.indptr, batch.indices, v, batch.rows, batch.cols)
+            torch.cuda.synchronize()
+            if it == W:
+                l0 = kernel_launches()
+            e0, e1, e2 = (torch.cuda.Event(enable_timing=True) for _ in range(3))
+            e0.record(stream)
+            U_S, th = add_cols_with_grad(h, bt, S)
+            L = (U_S * U_S * th).sum()
+            e1.record(stream)
+            (gv,) = torch.autograd.grad(L, v)
+            e2.record(stream)
+            torch.cuda.synchronize()
+            if it >= W:
+                fwd.append(e0.elapsed_time(e1)); bwd.append(e1.elapsed_time(e2))
+            grads = gv
+        launches = kernel_launches() - l0
+        code = h.status()
+        return dict(fwd_ms=float(np.mean(fwd)), bwd_ms=float(np.mean(bwd)), steps=K, status=code,
+                    launches_per_step=launches / K, grad=grads.cpu().numpy())
+
+    W = max(3, args.warmup)
+    K = args.steps if args.steps > 0 else 20
+    res = {"fp32_mixed": run("fp32", "mixed", W, K), "fp64_fp64": run("fp64", "fp64", W, K)}
+    head = res["fp32_mixed"]
+    t = (head["fwd_ms"] + head["bwd_ms"]) / 1e3
+    cpu = None
+    if not args.no_cpu:
+        # the oracle gradient from the oracle's own row step (cpu_baseline leg)
+        from oracle import backward, svlcov as osv
+        t0 = time.perf_counter()
+        st = osv.State.init(p["U"], p["sigma"], p["V"])
+        st.apply("rows", p["rows"])
+        U, sg, V = st.factors()
+        t1 = time.perf_counter()
+        ga = backward.grad_autograd(U, sg, b.indptr, b.indices, b.values, b.rows, S_rows)
+        t2 = time.perf_counter()
+        for r in res.values():
+            r["grad_rel_err_vs_oracle"] = float(np.linalg.norm(r["grad"] - ga) / np.linalg.norm(ga))
+        cpu = dict(value=b.rows / (t2 - t1), unit="differentiated update cols/s", cores=len(os.sched_getaffinity(0)),
+                   kind="oracle", sample="one forward + backward of the same column step (torch float64 autograd "
+                                         "of the dense step); the oracle's row step before it is not timed")
+    for r in res.values():
+        r.pop("grad")
+    line = dict(metric=METRIC + " [C5: forward + backward]", value=b.rows / t, unit="differentiated update cols/s",
+                n_gpus=1, steps=K, warmup=W, ms_per_step=t * 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32 storage, f32+f64 small steps, f64 adjoint", data="synthetic",
+                config=dict(workload=C5_WORKLOAD, global_batch=b.rows, l2="flushed (512 MB write) between steps",
+                            nnz=b.nnz, loss_rows=len(S_rows)),
+                paths=res, cpu_baseline=cpu, gpu_launches=int(round(head["launches_per_step"] * K)))
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
         return main_reference(args)
     if args.workload == "c4":
         return main_c4(args)
+    if args.workload == "c5":
+        return main_c5(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:
