@@ -321,37 +321,27 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
   launch_copy<TC>(SE, S, (int64_t)s * s, status, st);
   gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);        // S = S_E - C0^T C0
   TC tau = (TC)h->d.tau;
+  // Scratch of the blocked factorization (batches wider than one CTA's
+  // shared memory holds): pass 1 works on a copy of S in S2 (not yet
+  // formed), pass 2 on a copy of S2 in S (no longer needed); T1 is free
+  // during both.
   if (h->d.small == SVLCOV_SMALL_MIXED) {
     // Pass 1 in FP32 (its pivots resolve only down to ~eps32, hence the
     // FP32 deflation threshold), the pass-2 Gram in FP64, pass 2 in FP32 on
     // the small deviation from the identity (delta form).
     double* Sd = (double*)S;
     double tau1 = std::max(h->d.tau, 1e-6);
-    bool ok = launch_cholinv_smem<float, double, double, false>(Sd, s, (const double*)e2, (float)tau1, (double*)L1,
-                                                               (double*)Y1, sb.defl1, status, st);
-    if (!ok) {
-      launch_chol<double>(Sd, s, (const double*)e2, tau1, (double*)L1, sb.defl1, status, st);
-      launch_tri_inv<double>((double*)L1, s, sb.defl1, (double*)Y1, status, st);
-    }
+    launch_cholinv<float, double, false>(Sd, s, (const double*)e2, (float)tau1, (double*)L1, (double*)Y1, sb.defl1,
+                                         (double*)S2, (double*)T1, status, st);
     gemm<TC>(false, true, s, s, s, (TC)1, S, s, Y1, s, (TC)0, T1, s, status, st, TRI_B_UP);   // T1 = S Y1^T
     gemm<TC>(false, false, s, s, s, (TC)1, Y1, s, T1, s, (TC)0, S2, s, status, st, TRI_A_LO);  // S2 = Y1 S Y1^T
-    ok = launch_cholinv_smem<float, double, double, true>((double*)S2, s, nullptr, (float)h->d.tau, (double*)L2,
-                                                          (double*)Y2, sb.defl2, status, st);
-    if (!ok) {
-      launch_chol<double>((double*)S2, s, nullptr, h->d.tau, (double*)L2, sb.defl2, status, st);
-      launch_tri_inv<double>((double*)L2, s, sb.defl2, (double*)Y2, status, st);
-    }
+    launch_cholinv<float, double, true>((double*)S2, s, nullptr, (float)h->d.tau, (double*)L2, (double*)Y2,
+                                        sb.defl2, (double*)S, (double*)T1, status, st);
   } else {
-    if (!launch_cholinv_smem<TC, TC, TC, false>(S, s, e2, tau, L1, Y1, sb.defl1, status, st)) {
-      launch_chol<TC>(S, s, e2, tau, L1, sb.defl1, status, st);                            // S = L1 L1^T
-      launch_tri_inv<TC>(L1, s, sb.defl1, Y1, status, st);                                 // Y1 = L1^-1
-    }
+    launch_cholinv<TC, TC, false>(S, s, e2, tau, L1, Y1, sb.defl1, S2, T1, status, st);         // S = L1 L1^T, Y1 = L1^-1
     gemm<TC>(false, true, s, s, s, (TC)1, S, s, Y1, s, (TC)0, T1, s, status, st, TRI_B_UP);   // T1 = S Y1^T
     gemm<TC>(false, false, s, s, s, (TC)1, Y1, s, T1, s, (TC)0, S2, s, status, st, TRI_A_LO);  // S2 = Y1 S Y1^T
-    if (!launch_cholinv_smem<TC, TC, TC, false>(S2, s, nullptr, tau, L2, Y2, sb.defl2, status, st)) {
-      launch_chol<TC>(S2, s, nullptr, tau, L2, sb.defl2, status, st);                      // S2 = L2 L2^T
-      launch_tri_inv<TC>(L2, s, sb.defl2, Y2, status, st);
-    }
+    launch_cholinv<TC, TC, false>(S2, s, nullptr, tau, L2, Y2, sb.defl2, S, T1, status, st);    // S2 = L2 L2^T
   }
   gemm<TC>(true, true, s, s, s, (TC)1, L2, s, L1, s, (TC)0, R, s, status, st, TRI_A_UP | TRI_B_UP);  // R = L2^T L1^T
   gemm<TC>(true, true, s, s, s, (TC)1, Y1, s, Y2, s, (TC)0, X, s, status, st, TRI_A_UP | TRI_B_UP);  // X = Y1^T Y2^T

@@ -62,16 +62,14 @@ void gemm(bool ta, bool tb, int M, int N, int Kd, T alpha, const T* A, int lda, 
           T beta, T* C, int ldc, const int* status, cudaStream_t st, int tri = 0);
 enum { TRI_A_UP = 1, TRI_A_LO = 2, TRI_B_UP = 4, TRI_B_LO = 8 };
 size_t cholinv_smem_bytes(int s, size_t elem);
-template <typename T, typename SrcT, typename OutT, bool DELTA>
-bool launch_cholinv_smem(const SrcT* S, int s, const SrcT* ref, T tau, OutT* L, OutT* Y, unsigned char* defl,
-                         int* status, cudaStream_t st);
-template <typename T>
-void launch_syrk_sub(int s, int k, const T* C0, const T* SE, T* S, const int* status, cudaStream_t st);
-template <typename T>
-void launch_chol(const T* S, int s, const T* ref, T tau, T* L, unsigned char* defl, int* status,
-                 cudaStream_t st);
-template <typename T>
-void launch_tri_inv(const T* L, int s, const unsigned char* defl, T* Y, const int* status, cudaStream_t st);
+// Cholesky with deflation S = L L^T and Y = L^-1 (dropped rows and columns
+// zeroed), factor arithmetic in T on SrcT data: one CTA in shared memory when
+// the packed triangle fits, else blocked with GEMM panels and trailing
+// updates, using the scratch Awork and Twork (s x s each).  DELTA: S = I + A
+// with small A (the second CholeskyQR pass), factored in the delta form.
+template <typename T, typename SrcT, bool DELTA>
+void launch_cholinv(const SrcT* S, int s, const SrcT* ref, T tau, SrcT* L, SrcT* Y, unsigned char* defl,
+                    SrcT* Awork, SrcT* Twork, int* status, cudaStream_t st);
 template <typename T>
 void launch_build_K_add(const T* sigma, const T* C0, const T* R, int k, int s, T* K, const int* status,
                         cudaStream_t st);

@@ -134,6 +134,51 @@ def test_c2_like_bf16_storage():
     assert c["sin_u"] < 1e-2 and c["sin_v"] < 1e-2, c
 
 
+def _small_c3(n_users=20000, n_items=5000, k=32, s=512, n_batches=2):
+    p = synth.c3_problem(n_users=n_users, n_items=n_items, k=k, s=s, n_batches=n_batches, power_iters=2)
+    return p["U"], p["sigma"], p["V"], p["batches"]
+
+
+@pytest.mark.parametrize("storage,small,tol", [("fp64", "fp64", 1e-10), ("fp64", "mixed", 1e-7),
+                                               ("fp32", "mixed", 1e-5), ("bf16", "mixed", 1e-3)])
+def test_c3_like_wide_batches(storage, small, tol):
+    """Rating matrix (Zipf item popularity), users appended in batches of
+    s = 512: wider than the one-CTA shared-memory Cholesky in FP64 and in the
+    FP32 first pass, so the blocked factorization runs.  R of the first step
+    equals the oracle's (it is unique: positive diagonal)."""
+    U, s, V, ops = _small_c3()
+    vdt = torch.float64 if storage == "fp64" else torch.float32
+    idt = torch.float64 if storage == "fp64" else torch.float32
+    g = make_gpu(U, s, V, ops, storage=storage, small=small, init_dtype=idt)
+    st = osv.State.init(U, s, V)
+    for t, (kind, b) in enumerate(ops):
+        g.apply(kind, dev_batch(kind, b, vdt))
+        st.apply(kind, b)
+        if t == 0 and storage == "fp64":
+            Rg, Ro = g.intermediate(3), st.log[-1]["R"]
+            rtol = 1e-10 if small == "fp64" else 1e-7
+            assert np.max(np.abs(Rg - Ro)) < rtol * np.abs(Ro).max()
+    assert g.status() == 0
+    Ug, sg, Vg = (x.cpu().numpy() for x in g.get_factors())
+    c = compare(Ug, sg, Vg, st)
+    assert c["sigma"] < tol, c
+    stol = 1e-8 if tol < 1e-9 else 10 * tol
+    assert c["sin_u"] < stol and c["sin_v"] < stol, c
+
+
+def test_maximum_rank_and_batch_width():
+    """k = 128 and s = 1024 (the largest the library takes; K is 1152^2):
+    one add-rows step of a rating matrix, mixed small steps, FP32 factors."""
+    U, s, V, ops = _small_c3(n_users=40000, n_items=10000, k=128, s=1024, n_batches=1)
+    g, code, Ug, sg, Vg = run_gpu(U, s, V, ops, storage="fp32", small="mixed", values_dtype=torch.float32,
+                                  init_dtype=torch.float32)
+    assert code == 0
+    st = run_oracle(U, s, V, ops)
+    c = compare(Ug, sg, Vg, st)
+    assert c["sigma"] < 1e-5, c
+    assert c["sin_u"] < 1e-4 and c["sin_v"] < 1e-4, c
+
+
 def test_query_rows_and_determinism():
     U, s, V, ops = _mixed_problem(5)
     g1, c1, U1, s1, V1 = run_gpu(U, s, V, ops)
