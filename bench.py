@@ -46,9 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed node batches (0 = all after warm-up)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c4", "c5"],
-                    help="c2: graph node insertion (default, the headline); c4: 64 matrices, batched weight updates; "
-                         "c5: forward + backward of one differentiated column step")
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+                    help="c2: graph node insertion (default, the headline); c3: ratings, k=128, s=1024, BF16 vs "
+                         "FP32 factors; c4: 64 matrices, batched weight updates; c5: forward + backward of one "
+                         "differentiated column step")
     ap.add_argument("--N", type=int, default=100_000)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--s", type=int, default=256)
@@ -422,6 +423,106 @@ def main_c4(args):
 
 
 # ---------------------------------------------------------------------------
+C3_WORKLOAD = ("C3 ratings: 1,000,000 users x 50,000 items (Zipf 1.1 item popularity, ~20 ratings per user, "
+               "ratings 1..5), k=128, start on the first 500,000 users (2 power iterations), users appended by "
+               "add_rows in batches of s=1024 (K = 1152^2)")
+C3_GOLDEN = os.path.join(ROOT, "tests", "golden", "c3_oracle_sigma.json")
+
+
+def main_c3(args):
+    import torch
+    from paper_2401_09703_gb300 import SVLCOV, DeviceCSR, kernel_launches
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    W = max(3, args.warmup)
+    K = args.steps if args.steps > 0 else 20
+    p = synth.c3_problem(n_batches=W + K, power_iters=2)
+    bat = [DeviceCSR.from_host(b.indptr, b.indices, b.values, b.rows, b.cols, device=dev, values_dtype=torch.float32)
+           for _, b in p["batches"]]
+    m0, k = p["U"].shape
+    n = p["V"].shape[0]
+    max_s = max(b.rows for b in bat)
+    max_nnz = max(b.nnz for b in bat)
+    U0 = torch.as_tensor(p["U"], dtype=torch.float32, device=dev)
+    V0 = torch.as_tensor(p["V"], dtype=torch.float32, device=dev)
+    s0 = torch.as_tensor(p["sigma"], device=dev)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    golden = None
+    if os.path.exists(C3_GOLDEN):
+        gj = json.load(open(C3_GOLDEN))
+        if len(gj["sigma_after_batch"]) >= W + K:
+            golden = np.array(gj["sigma_after_batch"][W + K - 1])
+    stream = torch.cuda.current_stream()
+
+    def run(storage, profile=False, clocks=None):
+        h = SVLCOV(U0, s0, V0, max_m=m0 + (W + K) * max_s + 64, max_n=n + 64, max_s=max_s, max_nnz=max_nnz,
+                   storage=storage, small="mixed")
+        for b in bat[:W]:
+            h.add_rows(b)
+        torch.cuda.synchronize()
+        if profile:
+            h.profile(True)
+            h.profile_read(reset=True)
+        evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)) for _ in range(K)]
+        if clocks:
+            clocks.start()
+        l0 = kernel_launches()
+        units = 0
+        for i, b in enumerate(bat[W:W + K]):
+            flush.zero_()
+            evs[i][0].record(stream)
+            h.add_rows(b)
+            evs[i][1].record(stream)
+            units += b.rows
+        torch.cuda.synchronize()
+        ck = clocks.stop() if clocks else None
+        launches = kernel_launches() - l0
+        ms = [a.elapsed_time(c) for a, c in evs]
+        out = dict(value=units / (sum(ms) / 1e3), unit=UNIT, ms_per_step=float(np.mean(ms)), status=h.status(),
+                   resets=int(h.small_state()[3]), launches=launches, clocks=ck)
+        sg = h.sigma().cpu().numpy()
+        if golden is not None:
+            keep = golden > 1e-12 * golden[0]
+            out["sigma_rel_err_vs_oracle"] = float(np.max(np.abs(sg[keep] - golden[keep]) / golden[keep]))
+        if profile:
+            out["profile"] = h.profile_read()
+        del h
+        torch.cuda.empty_cache()
+        return out
+
+    res = dict(bf16=run("bf16", clocks=Clocks(0)), fp32=run("fp32"))
+    prof = run("bf16", profile=True)["profile"]
+    pr_n = k + max_s
+    sweeps = prof["svd_sweeps"] / max(prof["svd"][1], 1)
+    roof = roofline_svd(p, prof, "mixed", sweeps, pr_n)
+    roof["sweeps_per_launch"] = sweeps
+    cpu = None
+    if not args.no_cpu:
+        from oracle import svlcov as osv
+        st = osv.State.init(p["U"], p["sigma"], p["V"])
+        t0 = time.perf_counter()
+        done = 0
+        for kind, b in p["batches"]:
+            st.apply(kind, b)
+            done += 1
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        t = time.perf_counter() - t0
+        cpu = dict(value=done * max_s / t, unit=UNIT, cores=len(os.sched_getaffinity(0)), kind="oracle",
+                   sample=f"first {done} add_rows batches of the same trajectory, FP64 numpy/scipy")
+    head = res["bf16"]
+    phases = {kk: dict(ms_total=round(v[0], 3), calls=v[1]) for kk, v in prof.items() if kk != "svd_sweeps"}
+    line = dict(metric=METRIC + " [C3: BF16 vs FP32 factors]", value=head["value"], unit=UNIT, n_gpus=1, steps=K,
+                warmup=W, ms_per_step=head["ms_per_step"], higher_is_better=True, scaling="weak", vs_baseline=None,
+                dtype="bf16 storage, f32+f64 small steps", data="synthetic",
+                config=dict(workload=C3_WORKLOAD, global_batch=max_s, l2="flushed (512 MB write) between steps"),
+                paths=res, roofline=roof, phases_ms=phases, cpu_baseline=cpu, gpu_launches=int(head["launches"]),
+                clocks=head["clocks"])
+    print(json.dumps(line))
+    return 0
+
+
+# ---------------------------------------------------------------------------
 C5_WORKLOAD = ("C5 differentiated column step: C2's first node batch (Chung-Lu N=100000, k=64; the add_rows step "
                "first, untimed), then add_cols with its distinct non-empty update vectors (194 of s=256) "
                "differentiated for L = sum over 4096 existing nodes of ||U_new[r] Theta^1/2||^2; "
@@ -519,6 +620,8 @@ def main():
         return main_c4(args)
     if args.workload == "c5":
         return main_c5(args)
+    if args.workload == "c3":
+        return main_c3(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:
