@@ -191,6 +191,40 @@ int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host
 int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
                             size_t capacity_doubles, int32_t* rows, int32_t* cols, void* stream);
 
+/* ---- approximate augmented space (the -GKL and -RPI variants) -----------
+ * Appendix "Approximating the Augmented Space" and the appendix algorithms
+ * "Add columns / Update weights with approximated augmented space": instead
+ * of an orthonormal basis of the whole residual (I - U U^T) E (Algorithm 2,
+ * s vectors), an l-vector basis Q of a Golub-Kahan-Lanczos (Algorithm 9) or
+ * randomized power-iteration (Algorithm 10) subspace of it is built in
+ * SV-LCOV form, with P = Z^T Q; the step then takes SVD_k of
+ * [[Sigma, U^T E], [0, P^T]] ((k+l) x (k+s)) and folds it as Algorithm 3
+ * does.  Cost O(s^2 l + (k+l)^2 (k+s)) for the dense part instead of
+ * O(s^3 + (k+s)^3); an approximation unless l >= rank of the residual.
+ * Add rows is the same on A^T; update weights approximates both sides and
+ * takes SVD_k of diag(Sigma, 0) + [U^T D; P_D^T][V^T E; P_E^T]^T. */
+#define SVLCOV_APPROX_GKL 1
+#define SVLCOV_APPROX_RPI 2
+typedef struct {
+  int32_t method;       /* SVLCOV_APPROX_GKL or SVLCOV_APPROX_RPI                         */
+  int32_t l;            /* rank of the approximate space, 1 <= l <= s (the batch width)   */
+  int32_t t;            /* RPI: power iterations (>= 1); ignored by GKL                   */
+  const double* start;  /* device FP64: GKL's p_1 (s values; NULL = all ones) or RPI's    */
+                        /*   starting matrix (s x l column-major, required); the same     */
+                        /*   start serves both sides of a weight update                   */
+  void* work;           /* device scratch of svlcov_approx_work_bytes(h, l) bytes,        */
+                        /*   256-byte aligned                                             */
+} svlcov_approx;
+/* Scratch bytes for steps with rank l (0 on bad arguments; host only). */
+size_t svlcov_approx_work_bytes(const svlcov_handle* h, int32_t l);
+/* As svlcov_add_cols / svlcov_add_rows / svlcov_update_weights, with the
+ * approximate space `a` (INVALID_ARG for a bad method, l or missing start or
+ * work).  svlcov_add_cols_backward does not apply to these steps. */
+int svlcov_add_cols_approx(svlcov_handle* h, const svlcov_csr* Ec_T, const svlcov_approx* a, void* stream);
+int svlcov_add_rows_approx(svlcov_handle* h, const svlcov_csr* Er, const svlcov_approx* a, void* stream);
+int svlcov_update_weights_approx(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T,
+                                 const svlcov_approx* a, void* stream);
+
 /* Backward of the last add-columns step (Algorithm 3; the fold of Section
  * 3.2): the gradient of a loss L(U_new[S], Theta) with respect to the stored
  * values of that step's batch E_c, from the intermediates the step left in

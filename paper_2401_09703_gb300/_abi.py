@@ -22,6 +22,7 @@ SVLCOV_SMALL_FP64, SVLCOV_SMALL_FP32, SVLCOV_SMALL_MIXED = 0, 1, 2
 SVLCOV_MAX_K = 128
 SVLCOV_MAX_S = 1024
 SVLCOV_SMALL_SVD_STATIC_MAX_N = 256
+SVLCOV_APPROX_GKL, SVLCOV_APPROX_RPI = 1, 2
 
 
 class svlcov_csr(C.Structure):
@@ -42,6 +43,11 @@ class svlcov_init_desc(C.Structure):
 
 class svlcov_op(C.Structure):
     _fields_ = [("kind", C.c_int32), ("a", svlcov_csr), ("b", svlcov_csr)]
+
+
+class svlcov_approx(C.Structure):
+    _fields_ = [("method", C.c_int32), ("l", C.c_int32), ("t", C.c_int32), ("start", C.c_void_p),
+                ("work", C.c_void_p)]
 
 
 # name -> (restype, argtypes)
@@ -65,6 +71,11 @@ SIGNATURES = {
                                    C.c_void_p, C.c_void_p, C.c_void_p]),
     "svlcov_get_intermediate": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_size_t,
                                           C.POINTER(C.c_int32), C.POINTER(C.c_int32), C.c_void_p]),
+    "svlcov_approx_work_bytes": (C.c_size_t, [C.c_void_p, C.c_int32]),
+    "svlcov_add_cols_approx": (C.c_int, [C.c_void_p, C.POINTER(svlcov_csr), C.POINTER(svlcov_approx), C.c_void_p]),
+    "svlcov_add_rows_approx": (C.c_int, [C.c_void_p, C.POINTER(svlcov_csr), C.POINTER(svlcov_approx), C.c_void_p]),
+    "svlcov_update_weights_approx": (C.c_int, [C.c_void_p, C.POINTER(svlcov_csr), C.POINTER(svlcov_csr),
+                                               C.POINTER(svlcov_approx), C.c_void_p]),
     "svlcov_add_cols_backward_work_bytes": (C.c_size_t, [C.c_void_p]),
     "svlcov_add_cols_backward": (C.c_int, [C.c_void_p, C.POINTER(svlcov_csr), C.c_void_p, C.c_int32, C.c_void_p,
                                            C.c_void_p, C.c_void_p, C.c_void_p, C.c_void_p, C.c_double, C.c_void_p,

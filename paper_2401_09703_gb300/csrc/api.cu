@@ -303,9 +303,11 @@ extern "C" uint64_t svlcov_kernel_launches(void) { return launches_total(); }
 // projected factor X' and its small factor W, compute C0 = W^T X'^T E, the
 // residual Gram S = E^T E - C0^T C0, R = R2 R1 and X = R^-1 (with dropped
 // directions zeroed), and C_Q = C0 X (so that B = E X and Q = B - U C_Q).
+// Turning the batch into SV-LCOV form (Lemmas 1-2): validation, the grouped
+// view, C0 = W^T X'^T E, S_E = E^T E and the residual Gram S = S_E - C0^T C0.
 template <typename TS, typename TC>
-static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, const TS* Xp, const TC* W, SideBufs& sb,
-                          cudaStream_t st) {
+static void prepare_side(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, const TS* Xp, const TC* W, SideBufs& sb,
+                         cudaStream_t st) {
   int k = h->k, s = b.rows;
   int* status = h->status;
   h->prof.begin(PH_PREP, st);
@@ -316,10 +318,20 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
   h->prof.next(PH_GATHER, st);
   launch_gather_gram<TS, TC>(b, Xp, k, W, sb.sc, P, SE, C0, e2, status, st);
   h->prof.next(PH_CHOLQR, st);
-  TC *S = (TC*)sb.S, *L1 = (TC*)sb.L1, *Y1 = (TC*)sb.Y1, *T1 = (TC*)sb.T1, *S2 = (TC*)sb.S2;
-  TC *L2 = (TC*)sb.L2, *Y2 = (TC*)sb.Y2, *R = (TC*)sb.R, *X = (TC*)sb.X, *CQ = (TC*)sb.CQ;
+  TC* S = (TC*)sb.S;
   launch_copy<TC>(SE, S, (int64_t)s * s, status, st);
   gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);        // S = S_E - C0^T C0
+}
+
+template <typename TS, typename TC>
+static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, const TS* Xp, const TC* W, SideBufs& sb,
+                          cudaStream_t st) {
+  int k = h->k, s = b.rows;
+  int* status = h->status;
+  prepare_side<TS, TC>(h, b, d_len, Xp, W, sb, st);
+  TC *C0 = (TC*)sb.C0, *e2 = (TC*)sb.e2;
+  TC *S = (TC*)sb.S, *L1 = (TC*)sb.L1, *Y1 = (TC*)sb.Y1, *T1 = (TC*)sb.T1, *S2 = (TC*)sb.S2;
+  TC *L2 = (TC*)sb.L2, *Y2 = (TC*)sb.Y2, *R = (TC*)sb.R, *X = (TC*)sb.X, *CQ = (TC*)sb.CQ;
   TC tau = (TC)h->d.tau;
   // Scratch of the blocked factorization (batches wider than one CTA's
   // shared memory holds): pass 1 works on a copy of S in S2 (not yet
@@ -526,6 +538,309 @@ extern "C" int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, co
                            : dispatch_weights<double>(h, *D_T, *Em_T, st);
   if (rc == SVLCOV_OK) {
     h->last_op = 2;
+    h->last_s = D_T->rows;
+  }
+  return rc;
+}
+
+// ---------------------------------------------------------------------------
+// Approximate augmented space (the -GKL / -RPI variants, Appendix algorithms
+// "Add columns / Update weights with approximated augmented space").  The
+// caller's scratch holds, per projected side, the l-vector basis (W the
+// coefficients of Q = E W - U (C0 W), P = Z^T Q) and the step's small dense
+// matrices; the rest of the step uses the handle's workspace as the exact
+// step does.
+namespace {
+struct ApproxSide {
+  double *P, *W, *T, *T2, *W2, *TE, *Pm, *wr, *u, *ab, *G, *L, *Y, *Aw, *Tw, *e2, *Cq, *Lr;
+  unsigned char* defl;
+};
+struct ApproxBufs {
+  ApproxSide side[2];
+  double *M, *Lm, *Ym, *Awm, *Twm, *GL;
+  unsigned char* deflm;
+};
+void approx_layout(void* base, int k, int s, int l, ApproxBufs& ab, size_t* total) {
+  Carver c(base);
+  int64_t n = k + l;
+  for (int sd = 0; sd < 2; ++sd) {
+    ApproxSide& a = ab.side[sd];
+    a.P = c.take<double>((int64_t)s * l);
+    a.W = c.take<double>((int64_t)s * l);
+    a.T = c.take<double>((int64_t)s * l);
+    a.T2 = c.take<double>((int64_t)s * l);
+    a.W2 = c.take<double>((int64_t)s * l);
+    a.TE = c.take<double>((int64_t)s * l);
+    a.Pm = c.take<double>((int64_t)s * (l + 1));
+    a.wr = c.take<double>(s);
+    a.u = c.take<double>(s);
+    a.ab = c.take<double>(2 * l + 2);
+    a.G = c.take<double>((int64_t)l * l);
+    a.L = c.take<double>((int64_t)l * l);
+    a.Y = c.take<double>((int64_t)l * l);
+    a.Aw = c.take<double>((int64_t)l * l);
+    a.Tw = c.take<double>((int64_t)l * l);
+    a.e2 = c.take<double>(l);
+    a.Cq = c.take<double>((int64_t)k * l);
+    a.Lr = c.take<double>(n * s);
+    a.defl = c.take<unsigned char>(l);
+  }
+  ab.M = c.take<double>(n * n);
+  ab.Lm = c.take<double>(n * n);
+  ab.Ym = c.take<double>(n * n);
+  ab.Awm = c.take<double>(n * n);
+  ab.Twm = c.take<double>(n * n);
+  ab.GL = c.take<double>(n * k);
+  ab.deflm = c.take<unsigned char>(n);
+  *total = (c.off + 255) & ~(size_t)255;
+}
+}  // namespace
+
+// The l-vector basis of one projected side from its residual Gram sb.S:
+// GKL (Algorithm 9) or t RPI iterations (Algorithm 10) with an SV-LCOV QR
+// that is CholeskyQR2 on W^T S W (same R as Algorithm 2), pass-1 pivots
+// judged against the raw norms w^T S_E w (reading R8).
+template <typename TC>
+static void approx_basis(svlcov_handle* h, SideBufs& sb, int s, const svlcov_approx& a, ApproxSide& x,
+                         cudaStream_t st) {
+  const int l = a.l;
+  int* status = h->status;
+  TC *S = (TC*)sb.S, *SE = (TC*)sb.SE;
+  TC *P = (TC*)x.P, *W = (TC*)x.W, *T = (TC*)x.T;
+  const TC tau = (TC)h->d.tau;
+  if (a.method == SVLCOV_APPROX_GKL) {
+    const TC* p1 = nullptr;   // NULL: all ones
+    if (a.start) {            // the caller's FP64 start, in the small-step type (u is free until the first S w)
+      if (sizeof(TC) == 8) p1 = (const TC*)a.start;
+      else { launch_cast<double, float>(a.start, (float*)x.u, s, st); p1 = (const TC*)x.u; }
+    }
+    launch_gkl<TC>(S, s, l, p1, (TC*)x.Pm, W, (TC*)x.wr, (TC*)x.u, (TC*)x.ab, P, status, st);
+    return;
+  }
+  if (sizeof(TC) == 8) launch_copy<TC>((const TC*)a.start, P, (int64_t)s * l, status, st);
+  else launch_cast<double, float>(a.start, (float*)P, (int64_t)s * l, st);
+  TC *T2 = (TC*)x.T2, *W2 = (TC*)x.W2, *TE = (TC*)x.TE, *G = (TC*)x.G, *L = (TC*)x.L, *Y = (TC*)x.Y;
+  for (int it = 0; it < a.t; ++it) {
+    launch_mgs_cols<TC>(P, s, l, status, st);                                                   // P orthonormal
+    launch_copy<TC>(P, W, (int64_t)s * l, status, st);
+    gemm<TC>(false, false, s, l, s, (TC)1, S, s, W, s, (TC)0, T, s, status, st);               // T = S W
+    gemm<TC>(false, false, s, l, s, (TC)1, SE, s, W, s, (TC)0, TE, s, status, st);             // S_E W
+    launch_diag_quad<TC>(W, TE, s, l, (TC*)x.e2, status, st);                                  // |E w_j|^2
+    gemm<TC>(true, false, l, l, s, (TC)1, W, s, T, s, (TC)0, G, l, status, st);                // W^T S W
+    launch_cholinv<TC, TC, false>(G, l, (const TC*)x.e2, tau, L, Y, x.defl, (TC*)x.Aw, (TC*)x.Tw, status, st);
+    gemm<TC>(false, true, s, l, l, (TC)1, W, s, Y, l, (TC)0, W2, s, status, st, TRI_B_UP);     // W R1^-1
+    gemm<TC>(false, true, s, l, l, (TC)1, T, s, Y, l, (TC)0, T2, s, status, st, TRI_B_UP);     // S W R1^-1
+    gemm<TC>(true, false, l, l, s, (TC)1, W2, s, T2, s, (TC)0, G, l, status, st);              // pass 2 Gram
+    launch_cholinv<TC, TC, false>(G, l, nullptr, tau, L, Y, x.defl, (TC*)x.Aw, (TC*)x.Tw, status, st);
+    gemm<TC>(false, true, s, l, l, (TC)1, W2, s, Y, l, (TC)0, W, s, status, st, TRI_B_UP);     // W = W R^-1
+    gemm<TC>(false, true, s, l, l, (TC)1, T2, s, Y, l, (TC)0, P, s, status, st, TRI_B_UP);     // P = S W
+  }
+}
+
+// Fold of one projected side with an approximate basis: Xn = W_X (F[:k] -
+// C' F[k:]) with C' = C0 W (k x l), and Mt = (W F[k:] Xn^-1)^T, the rows added
+// to X' at the batch's touched rows (F has l + k rows, leading dimension ldf).
+template <typename TC>
+static void fold_projected_approx(svlcov_handle* h, SideBufs& sb, ApproxSide& x, const TC* Wx, const TC* Fbig,
+                                  int ldf, int s, int l, TC* Xtmp, TC* Wn, TC* Winv, int* reset_flag,
+                                  cudaStream_t st) {
+  int k = h->k;
+  int* status = h->status;
+  TC* Cq = (TC*)x.Cq;
+  gemm<TC>(false, false, k, l, s, (TC)1, (TC*)sb.C0, k, (TC*)x.W, s, (TC)0, Cq, k, status, st);     // C' = C0 W
+  launch_copy2d<TC>(Fbig, ldf, Xtmp, k, k, k, status, st);                                         // F[:k]
+  gemm<TC>(false, false, k, k, l, (TC)-1, Cq, k, Fbig + k, ldf, (TC)1, Xtmp, k, status, st);        // - C' F[k:]
+  gemm<TC>(false, false, k, k, k, (TC)1, Wx, k, Xtmp, k, (TC)0, Wn, k, status, st);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st);
+  gemm<TC>(false, false, s, k, l, (TC)1, (TC*)x.W, s, Fbig + k, ldf, (TC)0, (TC*)sb.Y, s, status, st);  // W F[k:]
+  gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
+}
+
+template <typename TS, typename TC>
+static int step_add_approx(svlcov_handle* h, const svlcov_csr& b, bool cols, const svlcov_approx& a,
+                           cudaStream_t st) {
+  const int k = h->k, s = b.rows, l = a.l, nl = k + l, ns = k + s;
+  int* status = h->status;
+  SideBufs& sb = h->side[0];
+  ApproxBufs ab;
+  size_t tot = 0;
+  approx_layout(a.work, k, s, l, ab, &tot);
+  TS* XpP = (TS*)(cols ? h->d.ubuf : h->d.vbuf);
+  TS* XpO = (TS*)(cols ? h->d.vbuf : h->d.ubuf);
+  TC* WP = (TC*)(cols ? h->Wu : h->Wv);
+  TC* WO = (TC*)(cols ? h->Wv : h->Wu);
+  TC* WPn = (TC*)(cols ? h->Wu_new : h->Wv_new);
+  TC* WOn = (TC*)(cols ? h->Wv_new : h->Wu_new);
+  TC* WPi = (TC*)(cols ? h->Wu_inv : h->Wv_inv);
+  TC* WOi = (TC*)(cols ? h->Wv_inv : h->Wu_inv);
+  int* rP = h->flags + (cols ? 0 : 1);
+  int* rO = h->flags + (cols ? 1 : 0);
+  int64_t rowsP = cols ? h->m : h->n, rowsO = cols ? h->n : h->m;
+  prepare_side<TS, TC>(h, b, rowsP, XpP, WP, sb, st);
+  approx_basis<TC>(h, sb, s, a, ab.side[0], st);
+  TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
+  h->prof.begin(PH_SVD, st);
+  // SVD_k of the (k+l) x (k+s) K through K K^T = L L^T: the left vectors and
+  // singular values of K are those of the square L; G = K^T F Theta^-1.
+  launch_build_K_rect<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)ab.side[0].P, k, s, l, K, status, st);
+  gemm<TC>(false, true, nl, nl, ns, (TC)1, K, nl, K, nl, (TC)0, (TC*)ab.M, nl, status, st);
+  launch_cholinv<TC, TC, false>((TC*)ab.M, nl, nullptr, (TC)0, (TC*)ab.Lm, (TC*)ab.Ym, ab.deflm, (TC*)ab.Awm,
+                                (TC*)ab.Twm, status, st);
+  int e = small_svd_step<TC>(h, (TC*)ab.Lm, nl, F, theta, (TC*)ab.GL, st);
+  if (e) return SVLCOV_ERR_CUDA;
+  gemm<TC>(true, false, ns, k, nl, (TC)1, K, nl, F, nl, (TC)0, G, ns, status, st);          // K^T F
+  launch_scale_cols<TC>(G, ns, ns, k, theta, status, st);                                       // Theta^-1
+  h->prof.next(PH_FOLD, st);
+  fold_projected_approx<TC>(h, sb, ab.side[0], WP, F, nl, s, l, (TC*)h->Xu, WPn, WPi, rP, st);
+  gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, ns, (TC)0, WOn, k, status, st);      // W_O G[:k]
+  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st);
+  gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, ns, (TC)0, (TC*)h->Nt, k, status, st);  // (G[k:] W_O^-1)^T
+  FiniteSet<TC> fs{};
+  fs.ptr[0] = theta; fs.count[0] = k;
+  fs.ptr[1] = (TC*)sb.Mt; fs.count[1] = (int64_t)k * s;
+  fs.ptr[2] = (TC*)h->Nt; fs.count[2] = (int64_t)k * s;
+  fs.ptr[3] = WPn; fs.count[3] = (int64_t)k * k;
+  fs.ptr[4] = WOn; fs.count[4] = (int64_t)k * k;
+  fs.n = 5;
+  h->prof.next(PH_APPLY, st);
+  launch_check_finite_multi<TC>(fs, status, st);
+  launch_reset<TS, TC>(XpP, rowsP, k, WPn, rP, status, st);
+  launch_scatter<TS, TC>(XpP, k, (TC*)sb.Mt, b.nnz, sb.sc, status, st);
+  launch_reset<TS, TC>(XpO, rowsO, k, WOn, rO, status, st);
+  launch_append<TS, TC>(XpO, rowsO, k, s, (TC*)h->Nt, status, st);
+  if (cols)
+    launch_commit<TC>((TC*)h->Wu, WPn, rP, (TC*)h->Wv, WOn, rO, (TC*)h->sigma, theta, k, h->counters, 0, s,
+                      h->resets, status, st);
+  else
+    launch_commit<TC>((TC*)h->Wu, WOn, rO, (TC*)h->Wv, WPn, rP, (TC*)h->sigma, theta, k, h->counters, s, 0,
+                      h->resets, status, st);
+  h->prof.end(st);
+  return last_launch();
+}
+
+template <typename TS, typename TC>
+static int step_weights_approx(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr& E, const svlcov_approx& a,
+                               cudaStream_t st) {
+  const int k = h->k, s = D.rows, l = a.l, nl = k + l;
+  int* status = h->status;
+  SideBufs& sd = h->side[0];
+  SideBufs& se = h->side[1];
+  ApproxBufs ab;
+  size_t tot = 0;
+  approx_layout(a.work, k, s, l, ab, &tot);
+  prepare_side<TS, TC>(h, D, h->m, (TS*)h->d.ubuf, (TC*)h->Wu, sd, st);
+  prepare_side<TS, TC>(h, E, h->n, (TS*)h->d.vbuf, (TC*)h->Wv, se, st);
+  approx_basis<TC>(h, sd, s, a, ab.side[0], st);
+  approx_basis<TC>(h, se, s, a, ab.side[1], st);
+  TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
+  h->prof.begin(PH_SVD, st);
+  launch_build_L_rect<TC>((TC*)sd.C0, (TC*)ab.side[0].P, k, s, l, (TC*)ab.side[0].Lr, status, st);
+  launch_build_L_rect<TC>((TC*)se.C0, (TC*)ab.side[1].P, k, s, l, (TC*)ab.side[1].Lr, status, st);
+  gemm<TC>(false, true, nl, nl, s, (TC)1, (TC*)ab.side[0].Lr, nl, (TC*)ab.side[1].Lr, nl, (TC)0, K, nl, status, st);
+  launch_add_diag<TC>(K, nl, (TC*)h->sigma, k, status, st);   // K = diag(S,0) + [C0D;PD^T][C0E;PE^T]^T
+  int e = small_svd_step<TC>(h, K, nl, F, theta, G, st);
+  if (e) return SVLCOV_ERR_CUDA;
+  h->prof.next(PH_FOLD, st);
+  fold_projected_approx<TC>(h, sd, ab.side[0], (TC*)h->Wu, F, nl, s, l, (TC*)h->Xu, (TC*)h->Wu_new,
+                            (TC*)h->Wu_inv, h->flags + 0, st);
+  fold_projected_approx<TC>(h, se, ab.side[1], (TC*)h->Wv, G, nl, s, l, (TC*)h->Xv, (TC*)h->Wv_new,
+                            (TC*)h->Wv_inv, h->flags + 1, st);
+  FiniteSet<TC> fs{};
+  fs.ptr[0] = theta; fs.count[0] = k;
+  fs.ptr[1] = (TC*)sd.Mt; fs.count[1] = (int64_t)k * s;
+  fs.ptr[2] = (TC*)se.Mt; fs.count[2] = (int64_t)k * s;
+  fs.ptr[3] = (TC*)h->Wu_new; fs.count[3] = (int64_t)k * k;
+  fs.ptr[4] = (TC*)h->Wv_new; fs.count[4] = (int64_t)k * k;
+  fs.n = 5;
+  h->prof.next(PH_APPLY, st);
+  launch_check_finite_multi<TC>(fs, status, st);
+  launch_reset<TS, TC>((TS*)h->d.ubuf, h->m, k, (TC*)h->Wu_new, h->flags + 0, status, st);
+  launch_scatter<TS, TC>((TS*)h->d.ubuf, k, (TC*)sd.Mt, D.nnz, sd.sc, status, st);
+  launch_reset<TS, TC>((TS*)h->d.vbuf, h->n, k, (TC*)h->Wv_new, h->flags + 1, status, st);
+  launch_scatter<TS, TC>((TS*)h->d.vbuf, k, (TC*)se.Mt, E.nnz, se.sc, status, st);
+  launch_commit<TC>((TC*)h->Wu, (TC*)h->Wu_new, h->flags + 0, (TC*)h->Wv, (TC*)h->Wv_new, h->flags + 1,
+                    (TC*)h->sigma, theta, k, h->counters, 0, 0, h->resets, status, st);
+  h->prof.end(st);
+  return last_launch();
+}
+
+static bool approx_ok(const svlcov_handle* h, const svlcov_approx* a, int s) {
+  if (!a || !a->work) return false;
+  if (a->method != SVLCOV_APPROX_GKL && a->method != SVLCOV_APPROX_RPI) return false;
+  if (a->l < 1 || a->l > s) return false;
+  if (a->method == SVLCOV_APPROX_RPI && (a->t < 1 || !a->start)) return false;
+  return true;
+}
+
+extern "C" size_t svlcov_approx_work_bytes(const svlcov_handle* h, int32_t l) {
+  if (!h || l < 1 || l > h->d.max_s) return 0;
+  ApproxBufs ab;
+  size_t tot = 0;
+  approx_layout(nullptr, h->k, (int)h->d.max_s, l, ab, &tot);
+  return tot;
+}
+
+template <typename TC>
+static int dispatch_add_approx(svlcov_handle* h, const svlcov_csr& b, bool cols, const svlcov_approx& a,
+                               cudaStream_t st) {
+  switch (h->d.storage) {
+    case SVLCOV_FP64: return step_add_approx<double, TC>(h, b, cols, a, st);
+    case SVLCOV_FP32: return step_add_approx<float, TC>(h, b, cols, a, st);
+    default: return step_add_approx<__nv_bfloat16, TC>(h, b, cols, a, st);
+  }
+}
+
+template <typename TC>
+static int dispatch_weights_approx(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr& E,
+                                   const svlcov_approx& a, cudaStream_t st) {
+  switch (h->d.storage) {
+    case SVLCOV_FP64: return step_weights_approx<double, TC>(h, D, E, a, st);
+    case SVLCOV_FP32: return step_weights_approx<float, TC>(h, D, E, a, st);
+    default: return step_weights_approx<__nv_bfloat16, TC>(h, D, E, a, st);
+  }
+}
+
+static int do_add_approx(svlcov_handle* h, const svlcov_csr* b, bool cols, const svlcov_approx* a, void* stream) {
+  if (!h || !csr_ok(b)) return SVLCOV_ERR_INVALID_ARG;
+  int64_t d_len = cols ? h->m : h->n;
+  if (b->cols != d_len) return SVLCOV_ERR_INVALID_ARG;
+  if (b->rows > h->d.max_s || b->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
+  if (cols ? (h->n + b->rows > h->d.max_n) : (h->m + b->rows > h->d.max_m)) return SVLCOV_ERR_CAPACITY;
+  if (b->rows == 0) return SVLCOV_OK;
+  if (!approx_ok(h, a, b->rows)) return SVLCOV_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = small_is_f32(h) ? dispatch_add_approx<float>(h, *b, cols, *a, st)
+                           : dispatch_add_approx<double>(h, *b, cols, *a, st);
+  if (rc == SVLCOV_OK) {
+    if (cols) h->n += b->rows;
+    else h->m += b->rows;
+    h->last_op = cols ? 3 : 4;   // no intermediates for the exact-step backward
+    h->last_s = b->rows;
+  }
+  return rc;
+}
+
+extern "C" int svlcov_add_cols_approx(svlcov_handle* h, const svlcov_csr* Ec_T, const svlcov_approx* a,
+                                      void* stream) {
+  return do_add_approx(h, Ec_T, true, a, stream);
+}
+
+extern "C" int svlcov_add_rows_approx(svlcov_handle* h, const svlcov_csr* Er, const svlcov_approx* a, void* stream) {
+  return do_add_approx(h, Er, false, a, stream);
+}
+
+extern "C" int svlcov_update_weights_approx(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T,
+                                            const svlcov_approx* a, void* stream) {
+  if (!h || !csr_ok(D_T) || !csr_ok(Em_T)) return SVLCOV_ERR_INVALID_ARG;
+  if (D_T->cols != h->m || Em_T->cols != h->n || D_T->rows != Em_T->rows) return SVLCOV_ERR_INVALID_ARG;
+  if (D_T->rows > h->d.max_s || D_T->nnz > h->d.max_nnz || Em_T->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
+  if (D_T->rows == 0) return SVLCOV_OK;
+  if (!approx_ok(h, a, D_T->rows)) return SVLCOV_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int rc = small_is_f32(h) ? dispatch_weights_approx<float>(h, *D_T, *Em_T, *a, st)
+                           : dispatch_weights_approx<double>(h, *D_T, *Em_T, *a, st);
+  if (rc == SVLCOV_OK) {
+    h->last_op = 5;
     h->last_s = D_T->rows;
   }
   return rc;
@@ -753,6 +1068,7 @@ extern "C" int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const vo
 extern "C" int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
                                        size_t capacity, int32_t* rows, int32_t* cols, void* stream) {
   if (!h || side < 0 || side > 1 || h->last_op < 0) return SVLCOV_ERR_INVALID_ARG;
+  if (h->last_op > 2) return SVLCOV_ERR_STATE;   // approximate steps keep other intermediates
   int k = h->k, s = h->last_s, n2 = k + s;
   const SideBufs& sb = h->side[side];
   const double* src = nullptr;

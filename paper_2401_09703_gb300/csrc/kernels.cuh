@@ -109,6 +109,25 @@ template <typename T> struct FiniteSet {
 template <typename T>
 void launch_check_finite_multi(const FiniteSet<T>& set, int* status, cudaStream_t st);
 
+// ---- approximate augmented space (-GKL / -RPI variants) ----------------------
+// GKL: l Lanczos steps on the residual Gram S (s x s) from p1 (NULL: all
+// ones); outputs W (s x l) coefficients of Q, P (s x l) = Z^T Q.  Scratch: Pm
+// (s x (l+1)), wr, u (s), ab (2l + 2).
+template <typename T>
+void launch_gkl(const T* S, int s, int l, const T* p1, T* Pm, T* W, T* wr, T* u, T* ab, T* P, const int* status,
+                cudaStream_t st);
+template <typename T>
+void launch_mgs_cols(T* P, int s, int l, const int* status, cudaStream_t st);
+template <typename T>
+void launch_diag_quad(const T* W, const T* TM, int s, int l, T* e2, const int* status, cudaStream_t st);
+template <typename T>
+void launch_build_K_rect(const T* sigma, const T* C0, const T* P, int k, int s, int l, T* K, const int* status,
+                         cudaStream_t st);
+template <typename T>
+void launch_build_L_rect(const T* C0, const T* P, int k, int s, int l, T* L, const int* status, cudaStream_t st);
+template <typename T>
+void launch_scale_cols(T* G, int rows, int ld, int k, const T* theta, const int* status, cudaStream_t st);
+
 // ---- backward of one add-columns step (FP64 small state) -------------------
 // Intermediates the forward step left in the workspace (column-major, FP64).
 struct BackwardInputs {

@@ -115,6 +115,50 @@ class SVLCOV:
         check(lib().svlcov_update_weights(self.h, C.byref(D.c()), C.byref(E.c()), _stream(stream)),
               "svlcov_update_weights")
 
+    # ---- approximate augmented space (-GKL / -RPI) -------------------------------
+    def _approx(self, method: str, l: int, start: Optional[torch.Tensor], t: int) -> _abi.svlcov_approx:
+        nb = lib().svlcov_approx_work_bytes(self.h, int(l))
+        if nb == 0:
+            raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_approx_work_bytes")
+        if getattr(self, "_ap_work", None) is None or self._ap_work.numel() < nb + 256:
+            self._ap_work = torch.empty(nb + 256, dtype=torch.uint8, device=self.device)
+        st = None
+        if start is not None:   # column-major s x l (or s) FP64 on the device
+            st = start.to(device=self.device, dtype=torch.float64)
+            st = (st.t() if st.dim() == 2 else st).contiguous()
+        self._ap_start = st
+        m = {"gkl": _abi.SVLCOV_APPROX_GKL, "rpi": _abi.SVLCOV_APPROX_RPI}[method]
+        return _abi.svlcov_approx(m, int(l), int(t), None if st is None else st.data_ptr(),
+                                  (self._ap_work.data_ptr() + 255) & ~255)
+
+    def add_cols_approx(self, batch: DeviceCSR, method: str, l: int, start: Optional[torch.Tensor] = None,
+                        t: int = 3, stream=None):
+        """Add columns with an approximate augmented space (start: GKL p_1 (s,)
+        or RPI starting matrix (s, l), row-major)."""
+        a = self._approx(method, l, start, t)
+        check(lib().svlcov_add_cols_approx(self.h, C.byref(batch.c()), C.byref(a), _stream(stream)),
+              "svlcov_add_cols_approx")
+
+    def add_rows_approx(self, batch: DeviceCSR, method: str, l: int, start: Optional[torch.Tensor] = None,
+                        t: int = 3, stream=None):
+        a = self._approx(method, l, start, t)
+        check(lib().svlcov_add_rows_approx(self.h, C.byref(batch.c()), C.byref(a), _stream(stream)),
+              "svlcov_add_rows_approx")
+
+    def update_weights_approx(self, D: DeviceCSR, E: DeviceCSR, method: str, l: int,
+                              start: Optional[torch.Tensor] = None, t: int = 3, stream=None):
+        a = self._approx(method, l, start, t)
+        check(lib().svlcov_update_weights_approx(self.h, C.byref(D.c()), C.byref(E.c()), C.byref(a),
+                                                 _stream(stream)), "svlcov_update_weights_approx")
+
+    def apply_approx(self, op: str, batch, method: str, l: int, start=None, t: int = 3, stream=None):
+        if op == "cols":
+            self.add_cols_approx(batch, method, l, start, t, stream)
+        elif op == "rows":
+            self.add_rows_approx(batch, method, l, start, t, stream)
+        else:
+            self.update_weights_approx(batch[0], batch[1], method, l, start, t, stream)
+
     def apply(self, op: str, batch, stream=None):
         if op == "cols":
             self.add_cols(batch, stream)
