@@ -104,6 +104,11 @@ typedef struct {
   double reset_threshold; /* cond_1 bound on U'', V'' (<= 0: default for storage) */
   int32_t jacobi_block;   /* tile width of the Jacobi SVD: columns per block,   */
                           /*   1..16 (<= 0: 16); a tuning knob, see autotune    */
+  int32_t reorth;         /* re-orthonormalise the projected factor X'W before  */
+                          /*   every `reorth`-th step and at init (W <- W       */
+                          /*   (W^T X'^T X' W)^-1/2); 0: default (every step    */
+                          /*   for BF16 storage, else never); < 0: never.       */
+                          /*   Needs small mode FP64 or MIXED.                  */
 } svlcov_init_desc;
 
 /* One item of a batched run: kind 0 = add columns (a), 1 = add rows (a),

@@ -38,7 +38,8 @@ class svlcov_init_desc(C.Structure):
                 ("U0", C.c_void_p), ("sigma0", C.c_void_p), ("V0", C.c_void_p), ("init_dtype", C.c_int32),
                 ("ubuf", C.c_void_p), ("vbuf", C.c_void_p),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
-                ("tau", C.c_double), ("reset_threshold", C.c_double), ("jacobi_block", C.c_int32)]
+                ("tau", C.c_double), ("reset_threshold", C.c_double), ("jacobi_block", C.c_int32),
+                ("reorth", C.c_int32)]
 
 
 class svlcov_op(C.Structure):

@@ -105,9 +105,17 @@ struct svlcov_handle {
   double *K, *F, *G, *theta, *Xu, *Xv, *Wu_new, *Wv_new, *Wu_inv, *Wv_inv, *Nt;
   void* jwork;
   void* rwork;  // FP64 refinement scratch of the mixed SVD
+  void* rowork = nullptr;  // re-orthonormalisation scratch (when enabled)
   // bookkeeping of the last step
   int last_op = -1, last_s = 0;
+  int64_t steps = 0;  // steps enqueued (schedules the re-orthonormalisation)
 };
+
+// Re-orthonormalisation of the projected factor(s) before a step (see the
+// init descriptor): on by default for BF16 storage, needs FP64 small factors.
+static bool reorth_on(const svlcov_init_desc& d) {
+  return d.small != SVLCOV_SMALL_FP32 && (d.reorth > 0 || (d.reorth == 0 && d.storage == SVLCOV_BF16));
+}
 
 static void layout(svlcov_handle* h, void* base, size_t* total) {
   const svlcov_init_desc& d = h->d;
@@ -173,6 +181,7 @@ static void layout(svlcov_handle* h, void* base, size_t* total) {
   h->Nt = c.take<double>(k * s);
   h->jwork = c.take<char>(jacobi_work_bytes((int)n2));
   h->rwork = c.take<char>(d.small == SVLCOV_SMALL_MIXED ? refine_work_bytes((int)n2, (int)k) : 256);
+  h->rowork = reorth_on(d) ? c.take<char>(reorth_work_bytes((int)k, std::max(d.max_m, d.max_n))) : nullptr;
   *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -184,6 +193,7 @@ static bool desc_ok(const svlcov_init_desc* d) {
   if (d->storage < SVLCOV_FP64 || d->storage > SVLCOV_BF16) return false;
   if (d->jacobi_block > 16) return false;
   if (d->small < SVLCOV_SMALL_FP64 || d->small > SVLCOV_SMALL_MIXED) return false;
+  if (d->reorth > 0 && d->small == SVLCOV_SMALL_FP32) return false;
   return true;
 }
 
@@ -207,6 +217,26 @@ extern "C" size_t svlcov_workspace_bytes(const svlcov_init_desc* d) {
   } while (0)
 
 static int last_launch() { return cudaGetLastError() == cudaSuccess ? SVLCOV_OK : SVLCOV_ERR_CUDA; }
+
+static void reorth_side(svlcov_handle* h, int side, cudaStream_t st) {
+  const void* X = side == 0 ? h->d.ubuf : h->d.vbuf;
+  int64_t rows = side == 0 ? h->m : h->n;
+  double* W = side == 0 ? h->Wu : h->Wv;
+  switch (h->d.storage) {
+    case SVLCOV_FP64: launch_reorth<double>((const double*)X, rows, h->k, W, h->rowork, h->status, st); break;
+    case SVLCOV_FP32: launch_reorth<float>((const float*)X, rows, h->k, W, h->rowork, h->status, st); break;
+    default: launch_reorth<__nv_bfloat16>((const __nv_bfloat16*)X, rows, h->k, W, h->rowork, h->status, st);
+  }
+}
+
+// sides: bit 0 U, bit 1 V
+static void maybe_reorth(svlcov_handle* h, int sides, cudaStream_t st) {
+  if (!h->rowork) return;
+  int every = h->d.reorth > 0 ? h->d.reorth : 1;
+  if (h->steps % every != 0) return;
+  if (sides & 1) reorth_side(h, 0, st);
+  if (sides & 2) reorth_side(h, 1, st);
+}
 
 template <typename TC>
 static void init_small(svlcov_handle* h, cudaStream_t st) {
@@ -255,6 +285,10 @@ extern "C" int svlcov_init(svlcov_handle** out, const svlcov_init_desc* d, void*
   if (d->storage == SVLCOV_FP64) init_factors<double>(h, st);
   else if (d->storage == SVLCOV_FP32) init_factors<float>(h, st);
   else init_factors<__nv_bfloat16>(h, st);
+  if (h->rowork) {   // the rounding of the start to the storage type
+    reorth_side(h, 0, st);
+    reorth_side(h, 1, st);
+  }
   if (last_launch() != SVLCOV_OK) {
     delete h;
     return SVLCOV_ERR_CUDA;
@@ -510,12 +544,14 @@ static int do_add(svlcov_handle* h, const svlcov_csr* b, bool cols, void* stream
   if (cols ? (h->n + b->rows > h->d.max_n) : (h->m + b->rows > h->d.max_m)) return SVLCOV_ERR_CAPACITY;
   if (b->rows == 0) return SVLCOV_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  maybe_reorth(h, cols ? 1 : 2, st);
   int rc = small_is_f32(h) ? dispatch_add<float>(h, *b, cols, st) : dispatch_add<double>(h, *b, cols, st);
   if (rc == SVLCOV_OK) {
     if (cols) h->n += b->rows;
     else h->m += b->rows;
     h->last_op = cols ? 0 : 1;
     h->last_s = b->rows;
+    ++h->steps;
   }
   return rc;
 }
@@ -534,11 +570,13 @@ extern "C" int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, co
   if (D_T->rows > h->d.max_s || D_T->nnz > h->d.max_nnz || Em_T->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
   if (D_T->rows == 0) return SVLCOV_OK;
   cudaStream_t st = (cudaStream_t)stream;
+  maybe_reorth(h, 3, st);
   int rc = small_is_f32(h) ? dispatch_weights<float>(h, *D_T, *Em_T, st)
                            : dispatch_weights<double>(h, *D_T, *Em_T, st);
   if (rc == SVLCOV_OK) {
     h->last_op = 2;
     h->last_s = D_T->rows;
+    ++h->steps;
   }
   return rc;
 }
@@ -809,6 +847,7 @@ static int do_add_approx(svlcov_handle* h, const svlcov_csr* b, bool cols, const
   if (b->rows == 0) return SVLCOV_OK;
   if (!approx_ok(h, a, b->rows)) return SVLCOV_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  maybe_reorth(h, cols ? 1 : 2, st);
   int rc = small_is_f32(h) ? dispatch_add_approx<float>(h, *b, cols, *a, st)
                            : dispatch_add_approx<double>(h, *b, cols, *a, st);
   if (rc == SVLCOV_OK) {
@@ -816,6 +855,7 @@ static int do_add_approx(svlcov_handle* h, const svlcov_csr* b, bool cols, const
     else h->m += b->rows;
     h->last_op = cols ? 3 : 4;   // no intermediates for the exact-step backward
     h->last_s = b->rows;
+    ++h->steps;
   }
   return rc;
 }
@@ -837,11 +877,13 @@ extern "C" int svlcov_update_weights_approx(svlcov_handle* h, const svlcov_csr* 
   if (D_T->rows == 0) return SVLCOV_OK;
   if (!approx_ok(h, a, D_T->rows)) return SVLCOV_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  maybe_reorth(h, 3, st);
   int rc = small_is_f32(h) ? dispatch_weights_approx<float>(h, *D_T, *Em_T, *a, st)
                            : dispatch_weights_approx<double>(h, *D_T, *Em_T, *a, st);
   if (rc == SVLCOV_OK) {
     h->last_op = 5;
     h->last_s = D_T->rows;
+    ++h->steps;
   }
   return rc;
 }

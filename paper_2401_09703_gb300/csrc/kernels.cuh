@@ -109,6 +109,11 @@ template <typename T> struct FiniteSet {
 template <typename T>
 void launch_check_finite_multi(const FiniteSet<T>& set, int* status, cudaStream_t st);
 
+// ---- re-orthonormalisation of a low-precision factor X'W ---------------------
+size_t reorth_work_bytes(int k, int64_t max_rows);
+template <typename TS>
+void launch_reorth(const TS* Xp, int64_t rows, int k, double* W, void* work, int* status, cudaStream_t st);
+
 // ---- approximate augmented space (-GKL / -RPI variants) ----------------------
 // GKL: l Lanczos steps on the residual Gram S (s x s) from p1 (NULL: all
 // ones); outputs W (s x l) coefficients of Q, P (s x l) = Z^T Q.  Scratch: Pm

@@ -64,7 +64,7 @@ class SVLCOV:
 
     def __init__(self, U0: torch.Tensor, sigma0: torch.Tensor, V0: torch.Tensor, *, max_m: int, max_n: int,
                  max_s: int, max_nnz: int, storage: str = "fp32", small: str = "mixed", tau: float = 0.0,
-                 reset_threshold: float = 0.0, jacobi_block: int = 0, stream=None):
+                 reset_threshold: float = 0.0, jacobi_block: int = 0, reorth: int = 0, stream=None):
         assert U0.is_cuda and V0.is_cuda and sigma0.is_cuda
         m, k = U0.shape
         n = V0.shape[0]
@@ -86,6 +86,7 @@ class SVLCOV:
         d.ubuf, d.vbuf = self.ubuf.data_ptr(), self.vbuf.data_ptr()
         d.tau, d.reset_threshold = tau, reset_threshold
         d.jacobi_block = jacobi_block
+        d.reorth = reorth
         nbytes = lib().svlcov_workspace_bytes(C.byref(d))
         if nbytes == 0:
             raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_workspace_bytes")

@@ -166,6 +166,33 @@ def test_c3_like_wide_batches(storage, small, tol):
     assert c["sin_u"] < stol and c["sin_v"] < stol, c
 
 
+def test_reorthonormalisation_keeps_fp64_parity():
+    """Forcing the re-orthonormalisation of the projected factor before every
+    step on FP64 storage changes nothing beyond rounding: U'W is orthonormal
+    to FP64 accuracy there, so the correction is ~eps."""
+    U, s, V, ops = _mixed_problem(4)
+    g, code, Ug, sg, Vg = run_gpu(U, s, V, ops, storage="fp64", small="fp64", reorth=1)
+    assert code == 0
+    c = compare(Ug, sg, Vg, run_oracle(U, s, V, ops))
+    assert c["sigma"] < 1e-10 and c["sin_u"] < 1e-8 and c["sin_v"] < 1e-8, c
+    assert checks.orth_err(Ug) < 1e-10 and checks.orth_err(Vg) < 1e-10
+
+
+def test_bf16_reorthonormalisation_reduces_drift():
+    """BF16 factors drift from orthonormal with every rounding; the default
+    re-orthonormalisation (every step) keeps Sigma closer to the oracle than
+    no correction, and within the BF16 target."""
+    U, s, V, ops = _small_c3(n_batches=4)
+    st = run_oracle(U, s, V, ops)
+    errs = {}
+    for ro in (-1, 0):
+        g, code, Ug, sg, Vg = run_gpu(U, s, V, ops, storage="bf16", small="mixed", values_dtype=torch.float32,
+                                      init_dtype=torch.float32, reorth=ro)
+        assert code == 0
+        errs[ro] = compare(Ug, sg, Vg, st)["sigma"]
+    assert errs[0] < errs[-1] and errs[0] < 1e-3, errs
+
+
 def test_maximum_rank_and_batch_width():
     """k = 128 and s = 1024 (the largest the library takes; K is 1152^2):
     one add-rows step of a rating matrix, mixed small steps, FP32 factors."""
