@@ -454,11 +454,24 @@ def main_c3(args):
             golden = np.array(gj["sigma_after_batch"][W + K - 1])
     stream = torch.cuda.current_stream()
 
-    def run(storage, profile=False, clocks=None):
+    # seeded starts of the approximate variants (inputs of the method), staged once
+    gst = synth.rng(1033)
+    starts = [(torch.as_tensor(gst.standard_normal(b.rows), device=dev),
+               torch.as_tensor(gst.standard_normal((b.rows, 10)), device=dev)) for b in bat]
+
+    def step(h, i, b, approx):
+        if approx is None:
+            h.add_rows(b)
+        elif approx == "gkl":
+            h.add_rows_approx(b, "gkl", 10, starts[i][0])
+        else:
+            h.add_rows_approx(b, "rpi", 10, starts[i][1], t=3)
+
+    def run(storage, profile=False, clocks=None, approx=None):
         h = SVLCOV(U0, s0, V0, max_m=m0 + (W + K) * max_s + 64, max_n=n + 64, max_s=max_s, max_nnz=max_nnz,
                    storage=storage, small="mixed")
-        for b in bat[:W]:
-            h.add_rows(b)
+        for i, b in enumerate(bat[:W]):
+            step(h, i, b, approx)
         torch.cuda.synchronize()
         if profile:
             h.profile(True)
@@ -471,7 +484,7 @@ def main_c3(args):
         for i, b in enumerate(bat[W:W + K]):
             flush.zero_()
             evs[i][0].record(stream)
-            h.add_rows(b)
+            step(h, W + i, b, approx)
             evs[i][1].record(stream)
             units += b.rows
         torch.cuda.synchronize()
@@ -490,7 +503,10 @@ def main_c3(args):
         torch.cuda.empty_cache()
         return out
 
-    res = dict(bf16=run("bf16", clocks=Clocks(0)), fp32=run("fp32"))
+    res = dict(bf16=run("bf16", clocks=Clocks(0)), fp32=run("fp32"),
+               gkl_l10_bf16=run("bf16", approx="gkl"), rpi_l10_t3_bf16=run("bf16", approx="rpi"))
+    for kk in ("gkl_l10_bf16", "rpi_l10_t3_bf16"):   # deviation from the exact update (the approximation)
+        res[kk]["note"] = "sigma_rel_err_vs_oracle is against the exact update's oracle: the approximation error"
     prof = run("bf16", profile=True)["profile"]
     pr_n = k + max_s
     sweeps = prof["svd_sweeps"] / max(prof["svd"][1], 1)
