@@ -66,6 +66,21 @@ def dist_env():
     return rank, world, local
 
 
+def max_over_ranks(t: float, world: int, device=None) -> float:
+    """The timed region's length as the job sees it: the slowest rank's."""
+    if world <= 1:
+        return t
+    import torch
+    tt = torch.tensor([t], dtype=torch.float64, device=device)
+    torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
+    return float(tt.item())
+
+
+def whole_job_rate(units_per_rank: int, world: int, t_max: float) -> float:
+    """Units all ranks processed (weak scaling: each rank runs its own replica) / slowest time."""
+    return world * units_per_rank / t_max
+
+
 def problem(args):
     return synth.c2_problem(N=args.N, k=args.k, s=args.s)
 
@@ -240,8 +255,11 @@ def roofline_svd(p, prof, small, sweeps_per_launch, n):
     achieved = flops / per_launch_s / 1e12
     # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
+    # DRAM bytes of one k_jacobi_cluster launch at n = 320 (read 857.6 KB: K and G in, all else in shared
+    # memory; write 0), from the ncu capture summarised in profiles/jacobi_cluster_n320_c2.md
+    traffic = 857600 if n == 320 else None
     return dict(bound="alu", achieved=round(achieved, 4), peak=round(peak, 2), unit="TFLOP/s",
-                frac=round(achieved / peak, 5), traffic=None, kernel="jacobi (Rayleigh-Ritz SVD_k of K)",
+                frac=round(achieved / peak, 5), traffic=traffic, kernel="jacobi (Rayleigh-Ritz SVD_k of K)",
                 flops_per_launch=flops, ms_per_launch=per_launch_s * 1e3,
                 peak_note="FP32 ALU peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz (no measured ALU peak)")
 
@@ -662,12 +680,8 @@ def main():
     e2e = run_e2e(p, p["batches"], torch, dev, W, K)
 
     # max over ranks of the timed device time
-    t_max = t_mixed
-    if world > 1:
-        tt = torch.tensor([t_mixed], device=dev, dtype=torch.float64)
-        torch.distributed.all_reduce(tt, op=torch.distributed.ReduceOp.MAX)
-        t_max = float(tt.item())
-    value = world * mixed["units"] / t_max
+    t_max = max_over_ranks(t_mixed, world, dev)
+    value = whole_job_rate(mixed["units"], world, t_max)
 
     # accuracy against the stored FP64 oracle trajectory (full default run only)
     err = dict(mixed=None, plain=None)
