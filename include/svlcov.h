@@ -192,7 +192,8 @@ int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host
  * synchronises).  which: 0 = P = X'^T E (k x s), 1 = S_E = E^T E (s x s),
  * 2 = C0 (k x s), 3 = R (s x s), 4 = K ((k+s) x (k+s)), 5 = Theta (k),
  * 6 = F ((k+s) x k), 7 = G ((k+s) x k).  side selects D (0) or E (1) for a
- * weight update.  Column-major; *rows, *cols receive the shape. */
+ * weight update.  Column-major; *rows, *cols receive the shape.  Only after
+ * an exact step (ERR_STATE after an approximate-space step). */
 int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t side, double* host_out,
                             size_t capacity_doubles, int32_t* rows, int32_t* cols, void* stream);
 

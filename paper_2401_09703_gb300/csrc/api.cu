@@ -102,7 +102,7 @@ struct svlcov_handle {
   double *Wu, *Wv, *sigma;
   // step scratch
   SideBufs side[2];
-  double *K, *F, *G, *theta, *Xu, *Xv, *Wu_new, *Wv_new, *Wu_inv, *Wv_inv, *Nt;
+  double *K, *F, *G, *theta, *Xu, *Xv, *Wu_new, *Wv_new, *Wu_inv, *Wv_inv, *Nt, *Itmp;
   void* jwork;
   void* rwork;  // FP64 refinement scratch of the mixed SVD
   void* rowork = nullptr;  // re-orthonormalisation scratch (when enabled)
@@ -179,6 +179,7 @@ static void layout(svlcov_handle* h, void* base, size_t* total) {
   h->Wu_inv = c.take<double>(k * k);
   h->Wv_inv = c.take<double>(k * k);
   h->Nt = c.take<double>(k * s);
+  h->Itmp = c.take<double>(2 * k * k);
   h->jwork = c.take<char>(jacobi_work_bytes((int)n2));
   h->rwork = c.take<char>(d.small == SVLCOV_SMALL_MIXED ? refine_work_bytes((int)n2, (int)k) : 256);
   h->rowork = reorth_on(d) ? c.take<char>(reorth_work_bytes((int)k, std::max(d.max_m, d.max_n))) : nullptr;
@@ -405,7 +406,7 @@ static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC
   launch_copy2d<TC>(Fbig, n2, Xtmp, k, k, k, status, st);                                             // Fk
   gemm<TC>(false, false, k, k, s, (TC)-1, (TC*)sb.CQ, k, Fbig + k, n2, (TC)1, Xtmp, k, status, st);  // - C_Q Fs
   gemm<TC>(false, false, k, k, k, (TC)1, W, k, Xtmp, k, (TC)0, Wn, k, status, st);
-  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, (TC*)h->Itmp);
   gemm<TC>(false, false, s, k, s, (TC)1, (TC*)sb.X, s, Fbig + k, n2, (TC)0, (TC*)sb.Y, s, status, st);
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
@@ -446,7 +447,7 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   h->prof.next(PH_FOLD, st);
   fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, st);
   gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, st);      // W_O G[:k]
-  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st);
+  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st, (TC*)h->Itmp);
   gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, n2, (TC)0, (TC*)h->Nt, k, status, st);  // (G[k:] W_O^-1)^T
   FiniteSet<TC> fs{};
   fs.ptr[0] = theta; fs.count[0] = k;
@@ -689,7 +690,7 @@ static void fold_projected_approx(svlcov_handle* h, SideBufs& sb, ApproxSide& x,
   launch_copy2d<TC>(Fbig, ldf, Xtmp, k, k, k, status, st);                                         // F[:k]
   gemm<TC>(false, false, k, k, l, (TC)-1, Cq, k, Fbig + k, ldf, (TC)1, Xtmp, k, status, st);        // - C' F[k:]
   gemm<TC>(false, false, k, k, k, (TC)1, Wx, k, Xtmp, k, (TC)0, Wn, k, status, st);
-  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, (TC*)h->Itmp);
   gemm<TC>(false, false, s, k, l, (TC)1, (TC*)x.W, s, Fbig + k, ldf, (TC)0, (TC*)sb.Y, s, status, st);  // W F[k:]
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
@@ -731,7 +732,7 @@ static int step_add_approx(svlcov_handle* h, const svlcov_csr& b, bool cols, con
   h->prof.next(PH_FOLD, st);
   fold_projected_approx<TC>(h, sb, ab.side[0], WP, F, nl, s, l, (TC*)h->Xu, WPn, WPi, rP, st);
   gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, ns, (TC)0, WOn, k, status, st);      // W_O G[:k]
-  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st);
+  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st, (TC*)h->Itmp);
   gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, ns, (TC)0, (TC*)h->Nt, k, status, st);  // (G[k:] W_O^-1)^T
   FiniteSet<TC> fs{};
   fs.ptr[0] = theta; fs.count[0] = k;

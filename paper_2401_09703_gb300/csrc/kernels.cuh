@@ -85,8 +85,12 @@ int launch_mixed_svd(const double* K, int n, int k, double* F, double* theta, do
 template <typename T>
 int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st,
                   int64_t* sweep_total = nullptr, int bcap = 0);
+// Guarded k x k inverse (Winv = I and *do_reset = 1 when W is singular or
+// cond_1(W) > thr).  tmp (2 k^2, may be NULL): scratch of the FP32 +
+// Newton form used for FP64 W when thr <= 1e3.
 template <typename T>
-void launch_inverse(const T* W, int k, T* Winv, double thr, int* do_reset, int* status, cudaStream_t st);
+void launch_inverse(const T* W, int k, T* Winv, double thr, int* do_reset, int* status, cudaStream_t st,
+                    T* tmp = nullptr);
 template <typename T>
 void launch_copy(const T* src, T* dst, int64_t count, const int* status, cudaStream_t st);
 template <typename T>
