@@ -423,8 +423,7 @@ def main_c4(args):
         return c4_handles(p, torch, dev, "mixed", blk)
 
     conc, blk, timings = autotune.tune(make_handles, lambda hs, r: items(hs, r, list(range(len(hs)))), sig,
-                                       cache_path=os.path.join(ROOT, "gpurun_out", "autotune_c4.json")
-                                       if os.path.isdir(os.path.join(ROOT, "gpurun_out")) else None)
+                                       cache_path=os.environ.get("SVLCOV_AUTOTUNE_CACHE"))
     res = dict(mixed_graph=run("mixed", conc, blk, True), mixed_streams=run("mixed", conc, blk, False),
                plain_sequential=run("fp32", 0, 16, False),
                k64_mixed_graph=run("mixed", conc, blk, True, only_k=64),
