@@ -46,10 +46,10 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed node batches (0 = all after warm-up)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "stream"],
                     help="c2: graph node insertion (default, the headline); c3: ratings, k=128, s=1024, BF16 vs "
                          "FP32 factors; c4: 64 matrices, batched weight updates; c5: forward + backward of one "
-                         "differentiated column step")
+                         "differentiated column step; stream: single-node updates, plain vs CUDA graph")
     ap.add_argument("--N", type=int, default=100_000)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--s", type=int, default=256)
@@ -645,6 +645,89 @@ def main_c5(args):
     return 0
 
 
+# ---------------------------------------------------------------------------
+STREAM_WORKLOAD = ("streaming node insertion: the C2 graph (Chung-Lu N=100000, k=64) with node batches of s=1 "
+                   "(add_rows then add_cols per node, K 65^2); plain launches vs the same steps captured in one "
+                   "CUDA graph")
+
+
+def main_stream(args):
+    import torch
+    from paper_2401_09703_gb300 import DeviceCSR, kernel_launches
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(0)
+    W = max(3, args.warmup)
+    K = args.steps if args.steps > 0 else 400
+    p = synth.c2_problem(s=1, n_batches=W + K)
+    bat = [(kind, DeviceCSR.from_host(b.indptr, b.indices, b.values, b.rows, b.cols, device=dev,
+                                      values_dtype=torch.float32)) for kind, b in p["batches"]]
+    max_nnz = max(b.nnz for _, b in bat)
+
+    def run(graph):
+        h = make_handle(p, torch, dev, "mixed", 1, max(max_nnz, 1))
+        for kind, b in bat[:2 * W]:
+            h.apply(kind, b)
+        torch.cuda.synchronize()
+        s = torch.cuda.Stream()
+        g = None
+        if graph:
+            g = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(s):
+                with torch.cuda.graph(g, stream=s):
+                    for kind, b in bat[2 * W:]:
+                        h.apply(kind, b, stream=s)
+        torch.cuda.synchronize()
+        e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        l0 = kernel_launches()
+        with torch.cuda.stream(s):
+            e0.record(s)
+            if g is not None:
+                g.replay()
+            else:
+                for kind, b in bat[2 * W:]:
+                    h.apply(kind, b, stream=s)
+            e1.record(s)
+        torch.cuda.synchronize()
+        ms = e0.elapsed_time(e1)
+        updates = 2 * K
+        out = dict(value=updates / (ms / 1e3), unit="updates/s", us_per_update=1e3 * ms / updates,
+                   status=h.status(), launches_per_update=(kernel_launches() - l0) / updates if not graph else None,
+                   sigma=h.sigma().cpu().numpy())
+        return out
+
+    res = dict(plain=run(False), graph=run(True))
+    same = bool(np.array_equal(res["plain"]["sigma"], res["graph"]["sigma"]))
+    cpu = None
+    if not args.no_cpu:
+        from oracle import svlcov as osv
+        st = osv.State.init(p["U"], p["sigma"], p["V"])
+        t0 = time.perf_counter()
+        done = 0
+        for kind, b in p["batches"]:
+            st.apply(kind, b)
+            done += 1
+            if time.perf_counter() - t0 > args.cpu_seconds:
+                break
+        t = time.perf_counter() - t0
+        cpu = dict(value=done / t, unit="updates/s", cores=len(os.sched_getaffinity(0)), kind="oracle",
+                   sample=f"first {done} single-node updates of the same sequence, FP64 numpy/scipy")
+        if done == len(p["batches"]):
+            so = st.sigma
+            keep = so > 1e-12 * so[0]
+            res["graph"]["sigma_rel_err_vs_oracle"] = float(np.max(np.abs(res["graph"]["sigma"][keep] - so[keep])
+                                                                  / so[keep]))
+    for r in res.values():
+        r.pop("sigma")
+    head = res["graph"]
+    line = dict(metric=METRIC + " [streaming, s=1]", value=head["value"], unit="updates/s", n_gpus=1, steps=K,
+                warmup=W, ms_per_step=head["us_per_update"] * 2 / 1e3, higher_is_better=True, scaling="weak",
+                vs_baseline=None, dtype="f32 storage, f32+f64 small steps", data="synthetic",
+                config=dict(workload=STREAM_WORKLOAD, global_batch=2, l2="factors resident (streaming)"),
+                paths=res, graph_equals_plain_bitwise=same, cpu_baseline=cpu)
+    print(json.dumps(line))
+    return 0
+
+
 def main():
     args = parse()
     if args.impl == "reference":
@@ -655,6 +738,8 @@ def main():
         return main_c5(args)
     if args.workload == "c3":
         return main_c3(args)
+    if args.workload == "stream":
+        return main_stream(args)
     import torch
     rank, world, local = dist_env()
     if world > 1:

@@ -205,10 +205,11 @@ void launch_group(const svlcov_csr& b, int logH, const SideScratch& w, int* stat
   note_launches(1);
   k_hash_clear<<<(int)cdiv(H, 256), 256, 0, st>>>(w.hkey, w.hcnt, H);
   int64_t nnz = b.nnz;
-  if (nnz > 0)
+  if (nnz > 0) {   // (no zero-block launch for an empty batch)
     note_launches(1);
     k_hash_insert<<<(int)cdiv(nnz, 256), 256, 0, st>>>(b.indices, nnz, logH, w.hkey, w.hcnt, w.slot,
                                                        w.rank_tmp, status);
+  }
   note_launches(1);
   k_group_scan<<<1, 1024, 0, st>>>(w.hcnt, H, w.hstart, w.occ, b.indptr, b.rows, w.chunk_off, w.chunk_row,
                                    w.counts, status);

@@ -75,3 +75,32 @@ def test_batched_run_captured_in_a_cuda_graph():
         Ua, sa, Va = (x.cpu().numpy() for x in a.get_factors())
         Ub, sb, Vb = (x.cpu().numpy() for x in b.get_factors())
         assert np.array_equal(Ua, Ub) and np.array_equal(sa, sb) and np.array_equal(Va, Vb)
+
+
+def test_steps_with_empty_batches_capture_in_a_cuda_graph():
+    """Single-vector steps, some with no nonzeros (isolated nodes of a graph
+    stream), captured in one CUDA graph: no zero-block launch may invalidate
+    the capture, and the replay equals the same steps run without a graph."""
+    p = synth.c2_problem(N=3000, k=8, s=1, n_batches=12, power_iters=2)
+    ops = p["batches"]
+    assert any(b.nnz == 0 for _, b in ops)
+    outs = []
+    for graph in (False, True):
+        g = make_gpu(p["U"], p["sigma"], p["V"], ops, storage="fp32", small="mixed", init_dtype=torch.float32)
+        bats = [(kind, dev_batch(kind, b, torch.float32)) for kind, b in ops]
+        st = torch.cuda.Stream()
+        if graph:
+            cg = torch.cuda.CUDAGraph()
+            with torch.cuda.stream(st):
+                with torch.cuda.graph(cg, stream=st):
+                    for kind, b in bats:
+                        g.apply(kind, b, stream=st)
+            cg.replay()
+        else:
+            for kind, b in bats:
+                g.apply(kind, b, stream=st)
+        torch.cuda.synchronize()
+        assert g.status() == 0
+        outs.append([x.cpu().numpy() for x in g.get_factors()])
+    for a, b in zip(outs[0], outs[1]):
+        assert np.array_equal(a, b)
