@@ -1,0 +1,68 @@
+"""Host-side logic that needs no GPU: the autotuner's cache, the seeded input
+generators the tests and the benchmark share, and the approximate-space
+scratch sizes of the C ABI (host-only queries)."""
+import json
+
+import numpy as np
+import pytest
+
+import synth
+
+
+def test_autotune_cache_hit_skips_timing(tmp_path):
+    from paper_2401_09703_gb300 import autotune
+    path = tmp_path / "tune.json"
+    key = autotune.cache_key("sig")
+    path.write_text(json.dumps({key: {"concurrency": 16, "jacobi_block": 8, "timings": {"16x8": 1.0}}}))
+    called = []
+    conc, blk, timings = autotune.tune(lambda b: called.append(b), lambda hs, r: [], "sig", cache_path=str(path))
+    assert (conc, blk) == (16, 8) and timings == {"16x8": 1.0}
+    assert not called
+
+
+def test_autotune_cache_ignores_unreadable_file(tmp_path):
+    from paper_2401_09703_gb300 import autotune
+    path = tmp_path / "bad.json"
+    path.write_text("{not json")
+    assert autotune.load_cache(str(path)) == {}
+    assert autotune.load_cache(None) == {}
+
+
+def test_generators_are_seeded_and_deterministic():
+    a = synth.c5_problem(N=1500, k=8, s=16, n_loss=100, power_iters=1)
+    b = synth.c5_problem(N=1500, k=8, s=16, n_loss=100, power_iters=1)
+    assert np.array_equal(a["cols"].indices, b["cols"].indices)
+    assert np.array_equal(a["S_rows"], b["S_rows"])
+    assert np.allclose(a["U"], b["U"])
+
+
+def test_distinct_nonempty_rows_drops_empty_and_repeated_vectors():
+    r = np.array([0, 0, 2, 2, 3, 4])
+    c = np.array([1, 5, 1, 5, 7, 2])
+    v = np.ones(6)
+    b = synth.csr_from_coo(r, c, v, 5, 10)          # rows 0 and 2 equal, row 1 empty
+    out = synth.distinct_nonempty_rows(b)
+    assert out.rows == 3
+    dense = out.dense()
+    assert dense.shape == (3, 10)
+    assert not np.any(np.all(dense == 0, axis=1))
+    assert len({tuple(row) for row in dense}) == 3
+
+
+def test_approx_scratch_size_is_host_only():
+    """svlcov_approx_work_bytes needs a handle; the workspace query for a
+    descriptor with the re-orthonormalisation on grows by the Gram scratch."""
+    import ctypes as C
+    from paper_2401_09703_gb300 import _abi
+    lib = _abi.lib()
+    d = _abi.svlcov_init_desc()
+    d.m, d.n, d.k, d.max_m, d.max_n, d.max_s, d.max_nnz = 100, 80, 8, 200, 200, 16, 64
+    d.storage, d.small = _abi.SVLCOV_BF16, _abi.SVLCOV_SMALL_MIXED
+    d.reorth = -1
+    off = lib.svlcov_workspace_bytes(C.byref(d))
+    d.reorth = 0       # default: on for BF16 storage
+    on = lib.svlcov_workspace_bytes(C.byref(d))
+    assert on > off > 0
+    d.small = _abi.SVLCOV_SMALL_FP32
+    d.reorth = 1       # needs FP64 small factors
+    assert lib.svlcov_workspace_bytes(C.byref(d)) == 0
