@@ -103,6 +103,8 @@ struct svlcov_handle {
   // step scratch
   SideBufs side[2];
   double *K, *F, *G, *theta, *Xu, *Xv, *Wu_new, *Wv_new, *Wu_inv, *Wv_inv, *Nt, *Itmp;
+  double *K2, *G2;   // K with the empty batch vectors' columns moved last, and its right vectors
+  int *perm, *nact;  // that column order (max_s) and k + the number of non-empty vectors
   void* jwork;
   void* rwork;  // FP64 refinement scratch of the mixed SVD
   void* rowork = nullptr;  // re-orthonormalisation scratch (when enabled)
@@ -180,6 +182,10 @@ static void layout(svlcov_handle* h, void* base, size_t* total) {
   h->Wv_inv = c.take<double>(k * k);
   h->Nt = c.take<double>(k * s);
   h->Itmp = c.take<double>(2 * k * k);
+  h->K2 = c.take<double>(n2 * n2);
+  h->G2 = c.take<double>(n2 * k);
+  h->perm = c.take<int>(s);
+  h->nact = c.take<int>(4);
   h->jwork = c.take<char>(jacobi_work_bytes((int)n2));
   h->rwork = c.take<char>(d.small == SVLCOV_SMALL_MIXED ? refine_work_bytes((int)n2, (int)k) : 256);
   h->rowork = reorth_on(d) ? c.take<char>(reorth_work_bytes((int)k, std::max(d.max_m, d.max_n))) : nullptr;
@@ -414,11 +420,13 @@ static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC
 // SVD_k of the Rayleigh-Ritz matrix: Jacobi in the small-step precision, or
 // FP32 sweeps + FP64 refinement in the mixed mode.
 template <typename TC>
-static int small_svd_step(svlcov_handle* h, const TC* K, int n2, TC* F, TC* theta, TC* G, cudaStream_t st) {
+static int small_svd_step(svlcov_handle* h, const TC* K, int n2, TC* F, TC* theta, TC* G, cudaStream_t st,
+                          const int* n_active = nullptr) {
   if (h->d.small == SVLCOV_SMALL_MIXED)
     return launch_mixed_svd((const double*)K, n2, h->k, (double*)F, (double*)theta, (double*)G, h->jwork, h->rwork,
-                            h->status, st, h->stats, h->d.jacobi_block);
-  return launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats, h->d.jacobi_block);
+                            h->status, st, h->stats, h->d.jacobi_block, n_active);
+  return launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats, h->d.jacobi_block,
+                           n_active);
 }
 
 template <typename TS, typename TC>
@@ -442,8 +450,14 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
   h->prof.begin(PH_SVD, st);
   launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
-  int e = small_svd_step<TC>(h, K, n2, F, theta, G, st);                                  // F, Theta, G = SVD_k(K)
+  // Empty update vectors give zero columns of K: move them last so that the
+  // Jacobi's tournament skips them (exact: their right vectors are unit vectors
+  // with zero singular values), then put G's rows back in the batch order.
+  launch_active_columns(b.indptr, s, k, h->perm, h->nact, status, st);
+  launch_permute_cols<TC>(K, n2, k, h->perm, (TC*)h->K2, status, st);
+  int e = small_svd_step<TC>(h, (TC*)h->K2, n2, F, theta, (TC*)h->G2, st, h->nact);     // F, Theta, G = SVD_k(K)
   if (e) return SVLCOV_ERR_CUDA;
+  launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);
   h->prof.next(PH_FOLD, st);
   fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, st);
   gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, st);      // W_O G[:k]

@@ -80,11 +80,24 @@ void launch_add_diag(T* K, int n, const T* sigma, int k, const int* status, cuda
 size_t jacobi_work_bytes(int n);
 int* jacobi_sweeps_ptr(void* work, int n, int elem);
 size_t refine_work_bytes(int n, int k);
+// n_active (optional, device): columns >= *n_active of K are zero; the
+// cluster form of the Jacobi then plays its tournament over the blocks
+// holding the active columns only.
 int launch_mixed_svd(const double* K, int n, int k, double* F, double* theta, double* G, void* jwork, void* rwork,
-                     int* status, cudaStream_t st, int64_t* sweep_total, int bcap = 0);
+                     int* status, cudaStream_t st, int64_t* sweep_total, int bcap = 0,
+                     const int* n_active = nullptr);
 template <typename T>
 int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st,
-                  int64_t* sweep_total = nullptr, int bcap = 0);
+                  int64_t* sweep_total = nullptr, int bcap = 0, const int* n_active = nullptr);
+// Empty update vectors to the end: perm (s) lists the non-empty batch
+// vectors first; *n_active = k + their number (device).
+void launch_active_columns(const int32_t* indptr, int s, int k, int* perm, int* n_active, const int* status,
+                           cudaStream_t st);
+template <typename T>
+void launch_permute_cols(const T* K, int n, int k, const int* perm, T* Kp, const int* status, cudaStream_t st);
+template <typename T>
+void launch_unpermute_rows(const T* Gp, int n, int k, int cols, const int* perm, T* G, const int* status,
+                           cudaStream_t st);
 // Guarded k x k inverse (Winv = I and *do_reset = 1 when W is singular or
 // cond_1(W) > thr).  tmp (2 k^2, may be NULL): scratch of the FP32 +
 // Newton form used for FP64 W when thr <= 1e3.
