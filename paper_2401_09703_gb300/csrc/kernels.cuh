@@ -88,7 +88,8 @@ int launch_mixed_svd(const double* K, int n, int k, double* F, double* theta, do
                      const int* n_active = nullptr);
 template <typename T>
 int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st,
-                  int64_t* sweep_total = nullptr, int bcap = 0, const int* n_active = nullptr);
+                  int64_t* sweep_total = nullptr, int bcap = 0, const int* n_active = nullptr,
+                  double stop_tol = 0.0);
 // Empty update vectors to the end: perm (s) lists the non-empty batch
 // vectors first; *n_active = k + their number (device).
 void launch_active_columns(const int32_t* indptr, int s, int k, int* perm, int* n_active, const int* status,
