@@ -246,21 +246,26 @@ def run_e2e(p, batches, torch, dev, W, K):
 
 
 def roofline_svd(p, prof, small, sweeps_per_launch, n):
-    """The dominant kernel is the Rayleigh-Ritz SVD (one-sided Jacobi).  Its
-    algorithmic work per sweep is n(n-1)/2 rotations x 9n FMA (one dot product
-    and two column-pair updates, of K and of G) = 9 n^2 (n-1) flop."""
-    ms, calls = prof["svd"]
+    """The dominant kernel is the Jacobi sweep kernel of the Rayleigh-Ritz
+    SVD.  Its algorithmic work per sweep is n(n-1)/2 rotations x 9n FMA (one
+    dot product and two column-pair updates, of K and of G) = 9 n^2 (n-1)
+    flop.  The duration is the kernel's own: CUDA events the library records
+    on its stream right around each sweep-kernel launch (profile phase
+    "jacobi_kernel"), averaged over the timed steps."""
+    ms, calls = prof["jacobi_kernel"]
     per_launch_s = ms / 1e3 / max(calls, 1)
     flops = sweeps_per_launch * 9.0 * n * n * (n - 1)
     achieved = flops / per_launch_s / 1e12
     # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    # DRAM bytes of one k_jacobi_cluster launch at n = 320 (read 857.6 KB: K and G in, all else in shared
+    # DRAM bytes of one k_jacobi_cluster launch at n = 320 (read 773.4 KB: K and G in, all else in shared
     # memory; write 0), from the ncu capture summarised in profiles/jacobi_cluster_n320_c2.md
-    traffic = 857600 if n == 320 else None
+    traffic = 773376 if n == 320 else None
+    svd_ms, svd_calls = prof["svd"]
     return dict(bound="alu", achieved=round(achieved, 4), peak=round(peak, 2), unit="TFLOP/s",
-                frac=round(achieved / peak, 5), traffic=traffic, kernel="jacobi (Rayleigh-Ritz SVD_k of K)",
+                frac=round(achieved / peak, 5), traffic=traffic, kernel="k_jacobi_cluster (Rayleigh-Ritz SVD_k of K)",
                 flops_per_launch=flops, ms_per_launch=per_launch_s * 1e3,
+                svd_phase_ms_per_call=svd_ms / max(svd_calls, 1),
                 peak_note="FP32 ALU peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz (no measured ALU peak)")
 
 
@@ -324,7 +329,7 @@ C4_WORKLOAD = ("C4 batched weight updates A + D E^T: 64 independent matrices, m 
                "k in {16,32,64,128}, s ~ U[8,128], 4 nnz per column of D and E; one step = one round of 64 updates")
 
 
-def c4_handles(p, torch, dev, small, jacobi_block, only_k=None):
+def c4_handles(p, torch, dev, small, jacobi_block, only_k=None, gemm_split=0):
     """Handles for the C4 matrices with seeded random orthonormal starts made
     on the device (the update step only sees the start factors)."""
     from paper_2401_09703_gb300 import SVLCOV
@@ -341,7 +346,7 @@ def c4_handles(p, torch, dev, small, jacobi_block, only_k=None):
         max_s = max(b[0].rows for _, b in mat["batches"])
         max_nnz = max(max(b[0].nnz, b[1].nnz) for _, b in mat["batches"])
         hs.append(SVLCOV(U.contiguous(), sg, V.contiguous(), max_m=m, max_n=n, max_s=max_s, max_nnz=max_nnz,
-                         storage="fp32", small=small, jacobi_block=jacobi_block))
+                         storage="fp32", small=small, jacobi_block=jacobi_block, gemm_split=gemm_split))
         del U, V
     return hs
 
@@ -367,7 +372,9 @@ def main_c4(args):
 
     def run(small, conc, blk, graph, only_k=None):
         sel = [i for i, mat in enumerate(p["mats"]) if only_k is None or mat["k"] == only_k]
-        hs = c4_handles(p, torch, dev, small, blk, only_k)
+        # handles run side by side (conc > 0) keep their FP64 products unsplit
+        split = 0 if conc == 0 else -1
+        hs = c4_handles(p, torch, dev, small, blk, only_k, split)
         for r in range(W):
             if conc == 0:
                 for h, i in zip(hs, sel):
@@ -390,7 +397,7 @@ def main_c4(args):
                 note = f"graph capture failed: {type(e).__name__}"
                 g = None
                 torch.cuda.synchronize()
-                hs = c4_handles(p, torch, dev, small, blk, only_k)
+                hs = c4_handles(p, torch, dev, small, blk, only_k, split)
                 for r in range(W):
                     batch_run(items(hs, r, sel), conc)
         torch.cuda.synchronize()
@@ -420,7 +427,7 @@ def main_c4(args):
     sig = "c4:" + ",".join(str(mat["k"]) for mat in p["mats"])
 
     def make_handles(blk):
-        return c4_handles(p, torch, dev, "mixed", blk)
+        return c4_handles(p, torch, dev, "mixed", blk, None, -1)
 
     conc, blk, timings = autotune.tune(make_handles, lambda hs, r: items(hs, r, list(range(len(hs)))), sig,
                                        cache_path=os.environ.get("SVLCOV_AUTOTUNE_CACHE"))

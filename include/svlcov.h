@@ -109,6 +109,12 @@ typedef struct {
                           /*   (W^T X'^T X' W)^-1/2); 0: default (every step    */
                           /*   for BF16 storage, else never); < 0: never.       */
                           /*   Needs small mode FP64 or MIXED.                  */
+  int32_t gemm_split;     /* FP64 small products that would leave SMs idle     */
+                          /*   split their K over thread-block clusters: 0     */
+                          /*   default (on); < 0 never (for handles that run   */
+                          /*   side by side, e.g. in svlcov_batch_run, where   */
+                          /*   the GPU is full anyway).  Results depend on it  */
+                          /*   (summation order), not on how a step is run.    */
 } svlcov_init_desc;
 
 /* One item of a batched run: kind 0 = add columns (a), 1 = add rows (a),
@@ -281,9 +287,10 @@ int svlcov_batch_run(svlcov_handle** handles, const svlcov_op* ops, int32_t n_op
  * grouping of the batch, 1 gather + Gram (turning into SV-LCOV form, Lemmas
  * 1-2), 2 CholeskyQR2 of the residual Gram (Algorithm 2), 3 the SVD_k of
  * the Rayleigh-Ritz matrix, 4 the small folds (Section 3.2), 5 the sparse
- * addition / append / reset / commit.  svlcov_profile_read synchronises on
- * the recorded events and returns accumulated milliseconds and counts per
- * phase (nphases <= 6); *svd_sweeps (may be NULL; synchronises the device)
+ * addition / append / reset / commit; a seventh entry, 6, times the Jacobi
+ * sweep kernel alone (nested inside phase 3).  svlcov_profile_read
+ * synchronises on the recorded events and returns accumulated milliseconds
+ * and counts per phase (nphases <= 7); *svd_sweeps (may be NULL; synchronises the device)
  * receives the number of Jacobi sweeps summed over all SVD launches since the
  * last reset; reset != 0 clears the totals. */
 int svlcov_profile_enable(svlcov_handle* h, int32_t enable);

@@ -43,7 +43,9 @@ int log2_ceil(int64_t v) {
 }  // namespace
 
 // Phase timing with CUDA events (enabled by svlcov_profile_enable).
-enum { PH_PREP = 0, PH_GATHER, PH_CHOLQR, PH_SVD, PH_FOLD, PH_APPLY, PH_COUNT };
+// PH_JACOBI is nested inside PH_SVD: the sweep kernel alone (no set-up,
+// extract or refinement), for the roofline of that kernel.
+enum { PH_PREP = 0, PH_GATHER, PH_CHOLQR, PH_SVD, PH_FOLD, PH_APPLY, PH_JACOBI, PH_COUNT };
 
 struct Prof {
   bool on = false;
@@ -73,13 +75,28 @@ struct Prof {
     end(st);
     begin(ph, st);
   }
+  // a nested record whose two events are recorded elsewhere (the Jacobi
+  // launcher records them around the sweep kernel)
+  bool nested(int ph, cudaEvent_t& a, cudaEvent_t& b) {
+    if (!on) return false;
+    Rec r{ph, nullptr, nullptr};
+    cudaEventCreate(&r.a);
+    cudaEventCreate(&r.b);
+    recs.push_back(r);
+    a = r.a;
+    b = r.b;
+    return true;
+  }
   void resolve() {
     for (auto& r : recs) {
       float t = 0.f;
       cudaEventSynchronize(r.b);
-      cudaEventElapsedTime(&t, r.a, r.b);
-      ms[r.ph] += t;
-      calls[r.ph] += 1;
+      if (cudaEventElapsedTime(&t, r.a, r.b) == cudaSuccess) {
+        ms[r.ph] += t;
+        calls[r.ph] += 1;
+      } else {
+        cudaGetLastError();   // a nested pair that was never recorded
+      }
       cudaEventDestroy(r.a);
       cudaEventDestroy(r.b);
     }
@@ -111,6 +128,13 @@ struct svlcov_handle {
   // bookkeeping of the last step
   int last_op = -1, last_s = 0;
   int64_t steps = 0;  // steps enqueued (schedules the re-orthonormalisation)
+};
+
+// The handle's split-K setting for the FP64 products it enqueues (restored
+// on leaving the entry point).
+struct SplitScope {
+  explicit SplitScope(const svlcov_handle* h) { set_gemm_split(!h || h->d.gemm_split >= 0); }
+  ~SplitScope() { set_gemm_split(true); }
 };
 
 // Re-orthonormalisation of the projected factor(s) before a step (see the
@@ -270,6 +294,7 @@ extern "C" int svlcov_init(svlcov_handle** out, const svlcov_init_desc* d, void*
   svlcov_handle* h = new (std::nothrow) svlcov_handle();
   if (!h) return SVLCOV_ERR_INVALID_ARG;
   h->d = *d;
+  SplitScope split_scope(h);
   h->k = d->k;
   h->m = d->m;
   h->n = d->n;
@@ -422,11 +447,17 @@ static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC
 template <typename TC>
 static int small_svd_step(svlcov_handle* h, const TC* K, int n2, TC* F, TC* theta, TC* G, cudaStream_t st,
                           const int* n_active = nullptr) {
+  cudaEvent_t ja = nullptr, jb = nullptr;
+  if (h->prof.nested(PH_JACOBI, ja, jb)) set_jacobi_events(ja, jb);
+  int e;
   if (h->d.small == SVLCOV_SMALL_MIXED)
-    return launch_mixed_svd((const double*)K, n2, h->k, (double*)F, (double*)theta, (double*)G, h->jwork, h->rwork,
-                            h->status, st, h->stats, h->d.jacobi_block, n_active);
-  return launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats, h->d.jacobi_block,
-                           n_active);
+    e = launch_mixed_svd((const double*)K, n2, h->k, (double*)F, (double*)theta, (double*)G, h->jwork, h->rwork,
+                         h->status, st, h->stats, h->d.jacobi_block, n_active);
+  else
+    e = launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats, h->d.jacobi_block,
+                          n_active);
+  set_jacobi_events(nullptr, nullptr);
+  return e;
 }
 
 template <typename TS, typename TC>
@@ -572,14 +603,17 @@ static int do_add(svlcov_handle* h, const svlcov_csr* b, bool cols, void* stream
 }
 
 extern "C" int svlcov_add_cols(svlcov_handle* h, const svlcov_csr* Ec_T, void* stream) {
+  SplitScope split_scope(h);
   return do_add(h, Ec_T, true, stream);
 }
 
 extern "C" int svlcov_add_rows(svlcov_handle* h, const svlcov_csr* Er, void* stream) {
+  SplitScope split_scope(h);
   return do_add(h, Er, false, stream);
 }
 
 extern "C" int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T, void* stream) {
+  SplitScope split_scope(h);
   if (!h || !csr_ok(D_T) || !csr_ok(Em_T)) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->cols != h->m || Em_T->cols != h->n || D_T->rows != Em_T->rows) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->rows > h->d.max_s || D_T->nnz > h->d.max_nnz || Em_T->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
@@ -877,15 +911,18 @@ static int do_add_approx(svlcov_handle* h, const svlcov_csr* b, bool cols, const
 
 extern "C" int svlcov_add_cols_approx(svlcov_handle* h, const svlcov_csr* Ec_T, const svlcov_approx* a,
                                       void* stream) {
+  SplitScope split_scope(h);
   return do_add_approx(h, Ec_T, true, a, stream);
 }
 
 extern "C" int svlcov_add_rows_approx(svlcov_handle* h, const svlcov_csr* Er, const svlcov_approx* a, void* stream) {
+  SplitScope split_scope(h);
   return do_add_approx(h, Er, false, a, stream);
 }
 
 extern "C" int svlcov_update_weights_approx(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T,
                                             const svlcov_approx* a, void* stream) {
+  SplitScope split_scope(h);
   if (!h || !csr_ok(D_T) || !csr_ok(Em_T)) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->cols != h->m || Em_T->cols != h->n || D_T->rows != Em_T->rows) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->rows > h->d.max_s || D_T->nnz > h->d.max_nnz || Em_T->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
@@ -1099,6 +1136,7 @@ extern "C" int svlcov_get_state(svlcov_handle* h, void* Up_host, void* Vp_host, 
 extern "C" int svlcov_set_state(svlcov_handle* h, int64_t m, int64_t n, const void* Up_host, const void* Vp_host,
                                 const double* Wu_host, const double* Wv_host, const double* sigma_host,
                                 void* stream) {
+  SplitScope split_scope(h);
   if (!h || m < 0 || n < 0 || m > h->d.max_m || n > h->d.max_n) return SVLCOV_ERR_INVALID_ARG;
   if (!Up_host || !Vp_host || !Wu_host || !Wv_host || !sigma_host) return SVLCOV_ERR_INVALID_ARG;
   CUDA_OK(cudaStreamSynchronize((cudaStream_t)stream));
@@ -1161,6 +1199,7 @@ extern "C" int svlcov_add_cols_backward(svlcov_handle* h, const svlcov_csr* E, c
                                         const double* U_pre_S, const double* U_pre_nnz, const double* dL_dU_S,
                                         const double* dL_dtheta, double* dL_dvalues, double gap, void* work,
                                         void* stream) {
+  SplitScope split_scope(h);
   if (!h || !csr_ok(E) || !work) return SVLCOV_ERR_INVALID_ARG;
   if (h->d.small != SVLCOV_SMALL_FP64 && h->d.small != SVLCOV_SMALL_MIXED) return SVLCOV_ERR_INVALID_ARG;
   if (h->last_op != 0 || E->rows != h->last_s) return SVLCOV_ERR_STATE;

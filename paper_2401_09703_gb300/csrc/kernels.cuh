@@ -86,6 +86,12 @@ size_t refine_work_bytes(int n, int k);
 int launch_mixed_svd(const double* K, int n, int k, double* F, double* theta, double* G, void* jwork, void* rwork,
                      int* status, cudaStream_t st, int64_t* sweep_total, int bcap = 0,
                      const int* n_active = nullptr);
+// Whether this host thread's FP64 products may split K over clusters (off
+// while svlcov_batch_run enqueues concurrent handles).
+void set_gemm_split(bool on);
+// Events the next Jacobi launches of this host thread record around their
+// sweep kernel (phase timing; nullptr: none).
+void set_jacobi_events(cudaEvent_t before, cudaEvent_t after);
 template <typename T>
 int launch_jacobi(const T* K, int n, int k, T* F, T* theta, T* G, void* work, int* status, cudaStream_t st,
                   int64_t* sweep_total = nullptr, int bcap = 0, const int* n_active = nullptr,

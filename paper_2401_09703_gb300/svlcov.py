@@ -64,7 +64,8 @@ class SVLCOV:
 
     def __init__(self, U0: torch.Tensor, sigma0: torch.Tensor, V0: torch.Tensor, *, max_m: int, max_n: int,
                  max_s: int, max_nnz: int, storage: str = "fp32", small: str = "mixed", tau: float = 0.0,
-                 reset_threshold: float = 0.0, jacobi_block: int = 0, reorth: int = 0, stream=None):
+                 reset_threshold: float = 0.0, jacobi_block: int = 0, reorth: int = 0, gemm_split: int = 0,
+                 stream=None):
         assert U0.is_cuda and V0.is_cuda and sigma0.is_cuda
         m, k = U0.shape
         n = V0.shape[0]
@@ -87,6 +88,7 @@ class SVLCOV:
         d.tau, d.reset_threshold = tau, reset_threshold
         d.jacobi_block = jacobi_block
         d.reorth = reorth
+        d.gemm_split = gemm_split
         nbytes = lib().svlcov_workspace_bytes(C.byref(d))
         if nbytes == 0:
             raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_workspace_bytes")
@@ -246,14 +248,15 @@ class SVLCOV:
         check(lib().svlcov_set_state(self.h, st["m"], st["n"], *[a.ctypes.data_as(C.c_void_p) for a in arrs],
                                      _stream(stream)), "svlcov_set_state")
 
-    PHASES = ("prep", "gather_gram", "cholqr2", "svd", "fold", "apply")
+    PHASES = ("prep", "gather_gram", "cholqr2", "svd", "fold", "apply", "jacobi_kernel")
 
     def profile(self, enable: bool = True):
         check(lib().svlcov_profile_enable(self.h, 1 if enable else 0), "svlcov_profile_enable")
 
     def profile_read(self, reset: bool = True) -> dict:
-        ms = np.zeros(6); calls = np.zeros(6, dtype=np.int64); sw = C.c_int64()
-        check(lib().svlcov_profile_read(self.h, ms.ctypes.data_as(C.c_void_p), calls.ctypes.data_as(C.c_void_p), 6,
+        n = len(self.PHASES)
+        ms = np.zeros(n); calls = np.zeros(n, dtype=np.int64); sw = C.c_int64()
+        check(lib().svlcov_profile_read(self.h, ms.ctypes.data_as(C.c_void_p), calls.ctypes.data_as(C.c_void_p), n,
                                         1 if reset else 0, C.byref(sw)), "svlcov_profile_read")
         out = {p: (float(ms[i]), int(calls[i])) for i, p in enumerate(self.PHASES)}
         out["svd_sweeps"] = int(sw.value)

@@ -18,8 +18,11 @@ def _problem(seed=7):
                             s_lo=3, s_hi=14, per_vec=4, power_iters=2)
 
 
-@pytest.mark.parametrize("storage,small,tol", [("fp64", "fp64", 1e-10), ("fp32", "mixed", 1e-5)])
-def test_batched_equals_sequential_and_oracle(storage, small, tol):
+@pytest.mark.parametrize("storage,small,tol,split", [("fp64", "fp64", 1e-10, 0), ("fp32", "mixed", 1e-5, 0),
+                                                     ("fp32", "mixed", 1e-5, -1), ("fp64", "mixed", 1e-7, -1)])
+def test_batched_equals_sequential_and_oracle(storage, small, tol, split):
+    """Batched and sequential runs of the same handles are bit-identical, with
+    the FP64 products split over clusters (default) or not (gemm_split < 0)."""
     from paper_2401_09703_gb300 import batch_run
     p = _problem()
     vd = torch.float64 if storage == "fp64" else torch.float32
@@ -27,8 +30,9 @@ def test_batched_equals_sequential_and_oracle(storage, small, tol):
     seq, bat, dev = [], [], []
     for mat in p["mats"]:
         ops = mat["batches"]
-        seq.append(make_gpu(mat["U"], mat["sigma"], mat["V"], ops, storage=storage, small=small, init_dtype=idt))
-        bat.append(make_gpu(mat["U"], mat["sigma"], mat["V"], ops, storage=storage, small=small, init_dtype=idt))
+        kw = dict(storage=storage, small=small, init_dtype=idt, gemm_split=split)
+        seq.append(make_gpu(mat["U"], mat["sigma"], mat["V"], ops, **kw))
+        bat.append(make_gpu(mat["U"], mat["sigma"], mat["V"], ops, **kw))
         dev.append([dev_batch(kind, b, vd) for kind, b in ops])
     for r in range(len(p["mats"][0]["batches"])):
         for h, d in zip(seq, dev):
