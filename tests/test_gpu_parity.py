@@ -59,6 +59,33 @@ def test_small_svd_matches_lapack(n, k, precision, tol):
     assert 0 < sweeps < 40
 
 
+def test_mixed_svd_close_pair_streaming_k():
+    """The Rayleigh-Ritz matrix of update 222 of the streaming node insertion
+    (C2 graph, s = 1), built by the oracle: its leading values include a pair
+    5e-4 apart (relative).  The mixed SVD (FP32 sweeps with the early stop,
+    three FP64 first-order steps) must reach FP64 accuracy on it; with a stop
+    of 1e-2 instead of 1e-3 the steps could not remove the coupling the sweeps
+    left between that pair (one value off by 1e-4)."""
+    from paper_2401_09703_gb300 import small_svd
+    p = synth.c2_problem(s=1, n_batches=112)
+    st = osv.State.init(p["U"], p["sigma"], p["V"])
+    for kind, b in p["batches"][:223]:
+        st.apply(kind, b)
+    # a rows step: the oracle logs K in the orientation of A, the GPU factors
+    # that of A^T (Algorithm 11 as Algorithm 3 on A^T), i.e. the transpose
+    K = np.ascontiguousarray(st.log[-1]["K"].T)
+    k = 64
+    Fo, tho, Go = dense.svd_k(K, k)
+    gaps = (tho[:-1] - tho[1:]) / tho[0]
+    assert gaps.min() < 1e-3            # the close pair is there
+    F, th, G, sweeps = small_svd(torch.as_tensor(K, device="cuda"), k, "mixed")
+    F, th, G = F.cpu().numpy(), th.cpu().numpy(), G.cpu().numpy()
+    assert checks.sigma_rel_err(th, tho) < 1e-12
+    assert np.max(np.abs(G.T @ G - np.eye(k))) < 1e-10
+    kp = checks.gapped_prefix(tho, 1e-6)
+    assert checks.max_sin_angle(G[:, :kp], Go[:, :kp]) < 1e-8
+
+
 @pytest.mark.parametrize("seed", [1, 2, 3])
 def test_mixed_trajectory_fp64(seed):
     """Add columns, add rows and weight updates in FP64: GPU = oracle."""
