@@ -120,6 +120,9 @@ struct svlcov_handle {
   // step scratch
   SideBufs side[2];
   double *K, *F, *G, *theta, *Xu, *Xv, *Wu_new, *Wv_new, *Wu_inv, *Wv_inv, *Nt, *Itmp;
+  double* Itmp2;     // the second side's inverse scratch (the two folds run concurrently)
+  cudaStream_t side_st = nullptr;   // the second fold's stream (forked from and joined into the step's)
+  cudaEvent_t ev_fork = nullptr, ev_join = nullptr;
   double *K2, *G2;   // K with the empty batch vectors' columns moved last, and its right vectors
   int *perm, *nact;  // that column order (max_s) and k + the number of non-empty vectors
   void* jwork;
@@ -206,6 +209,7 @@ static void layout(svlcov_handle* h, void* base, size_t* total) {
   h->Wv_inv = c.take<double>(k * k);
   h->Nt = c.take<double>(k * s);
   h->Itmp = c.take<double>(2 * k * k);
+  h->Itmp2 = c.take<double>(2 * k * k);
   h->K2 = c.take<double>(n2 * n2);
   h->G2 = c.take<double>(n2 * k);
   h->perm = c.take<int>(s);
@@ -325,6 +329,18 @@ extern "C" int svlcov_init(svlcov_handle** out, const svlcov_init_desc* d, void*
     delete h;
     return SVLCOV_ERR_CUDA;
   }
+  // the second fold's stream and its fork/join events; without them the two
+  // folds run one after the other on the step's stream
+  if (cudaStreamCreateWithFlags(&h->side_st, cudaStreamNonBlocking) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaEventCreateWithFlags(&h->ev_join, cudaEventDisableTiming) != cudaSuccess) {
+    cudaGetLastError();
+    if (h->side_st) cudaStreamDestroy(h->side_st);
+    if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+    if (h->ev_join) cudaEventDestroy(h->ev_join);
+    h->side_st = nullptr;
+    h->ev_fork = h->ev_join = nullptr;
+  }
   *out = h;
   return SVLCOV_OK;
 }
@@ -332,6 +348,9 @@ extern "C" int svlcov_init(svlcov_handle** out, const svlcov_init_desc* d, void*
 extern "C" void svlcov_destroy(svlcov_handle* h) {
   if (!h) return;
   h->prof.resolve();
+  if (h->side_st) cudaStreamDestroy(h->side_st);
+  if (h->ev_fork) cudaEventDestroy(h->ev_fork);
+  if (h->ev_join) cudaEventDestroy(h->ev_join);
   delete h;
 }
 
@@ -427,17 +446,45 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
   h->prof.end(st);
 }
 
+// The two folds of a step (the projected and the appended side, or the two
+// projected sides of a weight update) share no buffer but the status word, so
+// the second runs on the handle's side stream, forked from the step's stream
+// and joined back into it (capturable in a CUDA graph like any fork/join).
+// svlcov_batch_run turns the fork off while it enqueues: its handles already
+// run side by side, and the extra event calls slowed the host-bound eager
+// enqueue of many handles (148k -> 118k update vectors/s at 64 matrices).
+static thread_local bool t_side_fork = true;
+
+struct SideFork {
+  svlcov_handle* h;
+  cudaStream_t st;
+  bool on;
+  SideFork(svlcov_handle* hh, cudaStream_t s0) : h(hh), st(s0), on(hh->side_st != nullptr && t_side_fork) {
+    if (on) {
+      cudaEventRecord(h->ev_fork, st);
+      cudaStreamWaitEvent(h->side_st, h->ev_fork, 0);
+    }
+  }
+  cudaStream_t stream() const { return on ? h->side_st : st; }
+  ~SideFork() {
+    if (on) {
+      cudaEventRecord(h->ev_join, h->side_st);
+      cudaStreamWaitEvent(st, h->ev_join, 0);
+    }
+  }
+};
+
 // Fold of one projected side (Section 3.2): Xn = W (Fk - C_Q Fs), Winv, and
 // Mt = (X Fs Xn^-1)^T, the rows added to X' at the batch's touched rows.
 template <typename TC>
 static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC* Fbig, int n2, int s, TC* Xtmp,
-                           TC* Wn, TC* Winv, int* reset_flag, cudaStream_t st) {
+                           TC* Wn, TC* Winv, int* reset_flag, TC* itmp, cudaStream_t st) {
   int k = h->k;
   int* status = h->status;
   launch_copy2d<TC>(Fbig, n2, Xtmp, k, k, k, status, st);                                             // Fk
   gemm<TC>(false, false, k, k, s, (TC)-1, (TC*)sb.CQ, k, Fbig + k, n2, (TC)1, Xtmp, k, status, st);  // - C_Q Fs
   gemm<TC>(false, false, k, k, k, (TC)1, W, k, Xtmp, k, (TC)0, Wn, k, status, st);
-  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, (TC*)h->Itmp);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp);
   gemm<TC>(false, false, s, k, s, (TC)1, (TC*)sb.X, s, Fbig + k, n2, (TC)0, (TC*)sb.Y, s, status, st);
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
@@ -490,10 +537,14 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   if (e) return SVLCOV_ERR_CUDA;
   launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);
   h->prof.next(PH_FOLD, st);
-  fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, st);
-  gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, st);      // W_O G[:k]
-  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st, (TC*)h->Itmp);
-  gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, n2, (TC)0, (TC*)h->Nt, k, status, st);  // (G[k:] W_O^-1)^T
+  {
+    SideFork fk(h, st);
+    const cudaStream_t so = fk.stream();
+    gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, so);      // W_O G[:k]
+    launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, so, (TC*)h->Itmp2);
+    gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, n2, (TC)0, (TC*)h->Nt, k, status, so);  // (G[k:] W_O^-1)^T
+    fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, (TC*)h->Itmp, st);
+  }
   FiniteSet<TC> fs{};
   fs.ptr[0] = theta; fs.count[0] = k;
   fs.ptr[1] = (TC*)sb.Mt; fs.count[1] = (int64_t)k * s;
@@ -534,8 +585,13 @@ static int step_weights(svlcov_handle* h, const svlcov_csr& D, const svlcov_csr&
   int e = small_svd_step<TC>(h, K, n2, F, theta, G, st);
   if (e) return SVLCOV_ERR_CUDA;
   h->prof.next(PH_FOLD, st);
-  fold_projected<TC>(h, sd, (TC*)h->Wu, F, n2, s, (TC*)h->Xu, (TC*)h->Wu_new, (TC*)h->Wu_inv, h->flags + 0, st);
-  fold_projected<TC>(h, se, (TC*)h->Wv, G, n2, s, (TC*)h->Xv, (TC*)h->Wv_new, (TC*)h->Wv_inv, h->flags + 1, st);
+  {
+    SideFork fk(h, st);
+    fold_projected<TC>(h, se, (TC*)h->Wv, G, n2, s, (TC*)h->Xv, (TC*)h->Wv_new, (TC*)h->Wv_inv, h->flags + 1,
+                       (TC*)h->Itmp2, fk.stream());
+    fold_projected<TC>(h, sd, (TC*)h->Wu, F, n2, s, (TC*)h->Xu, (TC*)h->Wu_new, (TC*)h->Wu_inv, h->flags + 0,
+                       (TC*)h->Itmp, st);
+  }
   FiniteSet<TC> fs{};
   fs.ptr[0] = theta; fs.count[0] = k;
   fs.ptr[1] = (TC*)sd.Mt; fs.count[1] = (int64_t)k * s;
@@ -729,7 +785,7 @@ static void approx_basis(svlcov_handle* h, SideBufs& sb, int s, const svlcov_app
 // to X' at the batch's touched rows (F has l + k rows, leading dimension ldf).
 template <typename TC>
 static void fold_projected_approx(svlcov_handle* h, SideBufs& sb, ApproxSide& x, const TC* Wx, const TC* Fbig,
-                                  int ldf, int s, int l, TC* Xtmp, TC* Wn, TC* Winv, int* reset_flag,
+                                  int ldf, int s, int l, TC* Xtmp, TC* Wn, TC* Winv, int* reset_flag, TC* itmp,
                                   cudaStream_t st) {
   int k = h->k;
   int* status = h->status;
@@ -738,7 +794,7 @@ static void fold_projected_approx(svlcov_handle* h, SideBufs& sb, ApproxSide& x,
   launch_copy2d<TC>(Fbig, ldf, Xtmp, k, k, k, status, st);                                         // F[:k]
   gemm<TC>(false, false, k, k, l, (TC)-1, Cq, k, Fbig + k, ldf, (TC)1, Xtmp, k, status, st);        // - C' F[k:]
   gemm<TC>(false, false, k, k, k, (TC)1, Wx, k, Xtmp, k, (TC)0, Wn, k, status, st);
-  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, (TC*)h->Itmp);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp);
   gemm<TC>(false, false, s, k, l, (TC)1, (TC*)x.W, s, Fbig + k, ldf, (TC)0, (TC*)sb.Y, s, status, st);  // W F[k:]
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
@@ -778,10 +834,14 @@ static int step_add_approx(svlcov_handle* h, const svlcov_csr& b, bool cols, con
   gemm<TC>(true, false, ns, k, nl, (TC)1, K, nl, F, nl, (TC)0, G, ns, status, st);          // K^T F
   launch_scale_cols<TC>(G, ns, ns, k, theta, status, st);                                       // Theta^-1
   h->prof.next(PH_FOLD, st);
-  fold_projected_approx<TC>(h, sb, ab.side[0], WP, F, nl, s, l, (TC*)h->Xu, WPn, WPi, rP, st);
-  gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, ns, (TC)0, WOn, k, status, st);      // W_O G[:k]
-  launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, st, (TC*)h->Itmp);
-  gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, ns, (TC)0, (TC*)h->Nt, k, status, st);  // (G[k:] W_O^-1)^T
+  {
+    SideFork fk(h, st);
+    const cudaStream_t so = fk.stream();
+    gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, ns, (TC)0, WOn, k, status, so);      // W_O G[:k]
+    launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, so, (TC*)h->Itmp2);
+    gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, ns, (TC)0, (TC*)h->Nt, k, status, so);  // (G[k:] W_O^-1)^T
+    fold_projected_approx<TC>(h, sb, ab.side[0], WP, F, nl, s, l, (TC*)h->Xu, WPn, WPi, rP, (TC*)h->Itmp, st);
+  }
   FiniteSet<TC> fs{};
   fs.ptr[0] = theta; fs.count[0] = k;
   fs.ptr[1] = (TC*)sb.Mt; fs.count[1] = (int64_t)k * s;
@@ -828,10 +888,13 @@ static int step_weights_approx(svlcov_handle* h, const svlcov_csr& D, const svlc
   int e = small_svd_step<TC>(h, K, nl, F, theta, G, st);
   if (e) return SVLCOV_ERR_CUDA;
   h->prof.next(PH_FOLD, st);
-  fold_projected_approx<TC>(h, sd, ab.side[0], (TC*)h->Wu, F, nl, s, l, (TC*)h->Xu, (TC*)h->Wu_new,
-                            (TC*)h->Wu_inv, h->flags + 0, st);
-  fold_projected_approx<TC>(h, se, ab.side[1], (TC*)h->Wv, G, nl, s, l, (TC*)h->Xv, (TC*)h->Wv_new,
-                            (TC*)h->Wv_inv, h->flags + 1, st);
+  {
+    SideFork fk(h, st);
+    fold_projected_approx<TC>(h, se, ab.side[1], (TC*)h->Wv, G, nl, s, l, (TC*)h->Xv, (TC*)h->Wv_new,
+                              (TC*)h->Wv_inv, h->flags + 1, (TC*)h->Itmp2, fk.stream());
+    fold_projected_approx<TC>(h, sd, ab.side[0], (TC*)h->Wu, F, nl, s, l, (TC*)h->Xu, (TC*)h->Wu_new,
+                              (TC*)h->Wu_inv, h->flags + 0, (TC*)h->Itmp, st);
+  }
   FiniteSet<TC> fs{};
   fs.ptr[0] = theta; fs.count[0] = k;
   fs.ptr[1] = (TC*)sd.Mt; fs.count[1] = (int64_t)k * s;
@@ -983,6 +1046,7 @@ extern "C" int svlcov_batch_run(svlcov_handle** hs, const svlcov_op* ops, int32_
   for (int i = 0; i < P; ++i) CUDA_OK(cudaStreamWaitEvent(pool->streams[i], pool->fork, 0));
   std::unordered_map<svlcov_handle*, int> lane;  // handle -> its stream
   int next = 0;
+  t_side_fork = false;
   for (int32_t i = 0; i < n_ops && rc == SVLCOV_OK; ++i) {
     svlcov_handle* h = hs[i];
     if (!h) { rc = SVLCOV_ERR_INVALID_ARG; break; }
@@ -995,6 +1059,7 @@ extern "C" int svlcov_batch_run(svlcov_handle** hs, const svlcov_op* ops, int32_
     else if (op.kind == 2) rc = svlcov_update_weights(h, &op.a, &op.b, s2);
     else rc = SVLCOV_ERR_INVALID_ARG;
   }
+  t_side_fork = true;
   for (int i = 0; i < P; ++i) {  // join, also after an error
     CUDA_OK(cudaEventRecord(pool->done[i], pool->streams[i]));
     CUDA_OK(cudaStreamWaitEvent(st, pool->done[i], 0));
