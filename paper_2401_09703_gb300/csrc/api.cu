@@ -408,6 +408,35 @@ static void prepare_side(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, c
   gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);        // S = S_E - C0^T C0
 }
 
+// Independent branches of a step (the two folds, the two sides of the apply
+// phase, R and X = R^-1 of CholeskyQR2, the orthogonality product of the
+// refinement) share no buffer but the status word, so one of them runs on the
+// handle's side stream, forked from the step's stream and joined back into it
+// (capturable in a CUDA graph like any fork/join).
+// svlcov_batch_run turns the fork off while it enqueues: its handles already
+// run side by side, and the extra event calls slowed the host-bound eager
+// enqueue of many handles (148k -> 118k update vectors/s at 64 matrices).
+static thread_local bool t_side_fork = true;
+
+struct SideFork {
+  svlcov_handle* h;
+  cudaStream_t st;
+  bool on;
+  SideFork(svlcov_handle* hh, cudaStream_t s0) : h(hh), st(s0), on(hh->side_st != nullptr && t_side_fork) {
+    if (on) {
+      cudaEventRecord(h->ev_fork, st);
+      cudaStreamWaitEvent(h->side_st, h->ev_fork, 0);
+    }
+  }
+  cudaStream_t stream() const { return on ? h->side_st : st; }
+  ~SideFork() {
+    if (on) {
+      cudaEventRecord(h->ev_join, h->side_st);
+      cudaStreamWaitEvent(st, h->ev_join, 0);
+    }
+  }
+};
+
 template <typename TS, typename TC>
 static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, const TS* Xp, const TC* W, SideBufs& sb,
                           cudaStream_t st) {
@@ -440,39 +469,15 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
     gemm<TC>(false, false, s, s, s, (TC)1, Y1, s, T1, s, (TC)0, S2, s, status, st, TRI_A_LO);  // S2 = Y1 S Y1^T
     launch_cholinv<TC, TC, false>(S2, s, nullptr, tau, L2, Y2, sb.defl2, S, T1, status, st);    // S2 = L2 L2^T
   }
-  gemm<TC>(true, true, s, s, s, (TC)1, L2, s, L1, s, (TC)0, R, s, status, st, TRI_A_UP | TRI_B_UP);  // R = L2^T L1^T
-  gemm<TC>(true, true, s, s, s, (TC)1, Y1, s, Y2, s, (TC)0, X, s, status, st, TRI_A_UP | TRI_B_UP);  // X = Y1^T Y2^T
-  gemm<TC>(false, false, k, s, s, (TC)1, C0, k, X, s, (TC)0, CQ, k, status, st, TRI_B_UP);           // C_Q = C0 X
+  {
+    SideFork fk(h, st);
+    gemm<TC>(true, true, s, s, s, (TC)1, L2, s, L1, s, (TC)0, R, s, status, fk.stream(),
+             TRI_A_UP | TRI_B_UP);                                                                    // R = L2^T L1^T
+    gemm<TC>(true, true, s, s, s, (TC)1, Y1, s, Y2, s, (TC)0, X, s, status, st, TRI_A_UP | TRI_B_UP);  // X = Y1^T Y2^T
+    gemm<TC>(false, false, k, s, s, (TC)1, C0, k, X, s, (TC)0, CQ, k, status, st, TRI_B_UP);           // C_Q = C0 X
+  }
   h->prof.end(st);
 }
-
-// The two folds of a step (the projected and the appended side, or the two
-// projected sides of a weight update) share no buffer but the status word, so
-// the second runs on the handle's side stream, forked from the step's stream
-// and joined back into it (capturable in a CUDA graph like any fork/join).
-// svlcov_batch_run turns the fork off while it enqueues: its handles already
-// run side by side, and the extra event calls slowed the host-bound eager
-// enqueue of many handles (148k -> 118k update vectors/s at 64 matrices).
-static thread_local bool t_side_fork = true;
-
-struct SideFork {
-  svlcov_handle* h;
-  cudaStream_t st;
-  bool on;
-  SideFork(svlcov_handle* hh, cudaStream_t s0) : h(hh), st(s0), on(hh->side_st != nullptr && t_side_fork) {
-    if (on) {
-      cudaEventRecord(h->ev_fork, st);
-      cudaStreamWaitEvent(h->side_st, h->ev_fork, 0);
-    }
-  }
-  cudaStream_t stream() const { return on ? h->side_st : st; }
-  ~SideFork() {
-    if (on) {
-      cudaEventRecord(h->ev_join, h->side_st);
-      cudaStreamWaitEvent(st, h->ev_join, 0);
-    }
-  }
-};
 
 // Fold of one projected side (Section 3.2): Xn = W (Fk - C_Q Fs), Winv, and
 // Mt = (X Fs Xn^-1)^T, the rows added to X' at the batch's touched rows.
@@ -497,9 +502,12 @@ static int small_svd_step(svlcov_handle* h, const TC* K, int n2, TC* F, TC* thet
   cudaEvent_t ja = nullptr, jb = nullptr;
   if (h->prof.nested(PH_JACOBI, ja, jb)) set_jacobi_events(ja, jb);
   int e;
-  if (h->d.small == SVLCOV_SMALL_MIXED)
+  if (h->d.small == SVLCOV_SMALL_MIXED) {
+    const bool fk = t_side_fork && h->side_st;
     e = launch_mixed_svd((const double*)K, n2, h->k, (double*)F, (double*)theta, (double*)G, h->jwork, h->rwork,
-                         h->status, st, h->stats, h->d.jacobi_block, n_active);
+                         h->status, st, h->stats, h->d.jacobi_block, n_active, fk ? h->side_st : nullptr,
+                         fk ? h->ev_fork : nullptr, fk ? h->ev_join : nullptr);
+  }
   else
     e = launch_jacobi<TC>(K, n2, h->k, F, theta, G, h->jwork, h->status, st, h->stats, h->d.jacobi_block,
                           n_active);
@@ -554,10 +562,13 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   fs.n = 5;
   h->prof.next(PH_APPLY, st);
   launch_check_finite_multi<TC>(fs, status, st);
-  launch_reset<TS, TC>(XpP, rowsP, k, WPn, rP, status, st);   // only when the guard fired
-  launch_scatter<TS, TC>(XpP, k, (TC*)sb.Mt, b.nnz, sb.sc, status, st);
-  launch_reset<TS, TC>(XpO, rowsO, k, WOn, rO, status, st);
-  launch_append<TS, TC>(XpO, rowsO, k, s, (TC*)h->Nt, status, st);
+  {
+    SideFork fk(h, st);
+    launch_reset<TS, TC>(XpO, rowsO, k, WOn, rO, status, fk.stream());
+    launch_append<TS, TC>(XpO, rowsO, k, s, (TC*)h->Nt, status, fk.stream());
+    launch_reset<TS, TC>(XpP, rowsP, k, WPn, rP, status, st);   // only when the guard fired
+    launch_scatter<TS, TC>(XpP, k, (TC*)sb.Mt, b.nnz, sb.sc, status, st);
+  }
   if (cols)
     launch_commit<TC>((TC*)h->Wu, WPn, rP, (TC*)h->Wv, WOn, rO, (TC*)h->sigma, theta, k, h->counters, 0, s,
                       h->resets, status, st);

@@ -85,7 +85,8 @@ size_t refine_work_bytes(int n, int k);
 // holding the active columns only.
 int launch_mixed_svd(const double* K, int n, int k, double* F, double* theta, double* G, void* jwork, void* rwork,
                      int* status, cudaStream_t st, int64_t* sweep_total, int bcap = 0,
-                     const int* n_active = nullptr);
+                     const int* n_active = nullptr, cudaStream_t side = nullptr, cudaEvent_t ev_fork = nullptr,
+                     cudaEvent_t ev_join = nullptr);
 // Whether this host thread's FP64 products may split K over clusters (off
 // while svlcov_batch_run enqueues concurrent handles).
 void set_gemm_split(bool on);
