@@ -40,6 +40,15 @@ def load_cache(path: Optional[str]) -> dict:
     return {}
 
 
+def pick(timings: dict, candidates: Iterable[Tuple[int, int]], slack: float = 1.02) -> Tuple[int, int]:
+    """The candidate to keep: among those within `slack` of the fastest time,
+    the highest concurrency (then the fastest of those)."""
+    cands = list(candidates)
+    fastest = min(timings[f"{c}x{b}"] for c, b in cands)
+    near = [(c, b) for c, b in cands if timings[f"{c}x{b}"] <= slack * fastest]
+    return max(near, key=lambda cb: (cb[0], -timings[f"{cb[0]}x{cb[1]}"]))
+
+
 def _time_graph(hs, make_items, conc) -> Optional[float]:
     """One replay of batch 1 captured in a CUDA graph (ms), or None."""
     s = torch.cuda.Stream()
@@ -94,9 +103,7 @@ def tune(make_handles: Callable[[int], Sequence], make_items: Callable[[Sequence
             log(f"autotune concurrency={conc} jacobi_block={blk}: {ms:.2f} ms")
         del hs
         torch.cuda.empty_cache()
-    fastest = min(timings.values())
-    near = [(c, b) for c, b in candidates if timings[f"{c}x{b}"] <= 1.02 * fastest]
-    conc, blk = max(near, key=lambda cb: (cb[0], -timings[f"{cb[0]}x{cb[1]}"]))
+    conc, blk = pick(timings, candidates)
     best = (conc, blk, timings[f"{conc}x{blk}"])
     if cache_path:
         cache[key] = dict(concurrency=best[0], jacobi_block=best[1], timings=timings)

@@ -66,3 +66,16 @@ def test_approx_scratch_size_is_host_only():
     d.small = _abi.SVLCOV_SMALL_FP32
     d.reorth = 1       # needs FP64 small factors
     assert lib.svlcov_workspace_bytes(C.byref(d)) == 0
+
+
+def test_autotune_pick_prefers_concurrency_within_slack():
+    """Graph replays of many handles: within 2% of the fastest, the higher
+    concurrency wins (more independent branches); outside it, the fastest."""
+    from paper_2401_09703_gb300 import autotune
+    cands = [(8, 8), (8, 16), (32, 8), (64, 8), (64, 16)]
+    t = {"8x8": 27.2, "8x16": 27.1, "32x8": 15.6, "64x8": 15.9, "64x16": 15.7}
+    assert autotune.pick(t, cands) == (64, 16)          # 15.7 and 15.9 are within 2% of 15.6
+    t2 = dict(t, **{"64x8": 17.0, "64x16": 16.5})
+    assert autotune.pick(t2, cands) == (32, 8)          # the 64-lane times are 6% slower
+    t3 = {"8x8": 10.0, "8x16": 12.0, "32x8": 20.0, "64x8": 20.0, "64x16": 20.0}
+    assert autotune.pick(t3, cands) == (8, 8)
