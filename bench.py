@@ -56,6 +56,8 @@ def parse():
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--jacobi-block", type=int, default=0,
+                    help="columns per Jacobi block of the C2/streaming handles (0: the library default)")
     return ap.parse_args()
 
 
@@ -139,13 +141,17 @@ def stage(batches, torch, dev):
     return out
 
 
+JACOBI_BLOCK = 0   # --jacobi-block
+
+
 def make_handle(p, torch, dev, small, max_s, max_nnz):
     from paper_2401_09703_gb300 import SVLCOV
     U = torch.as_tensor(p["U"], dtype=torch.float32, device=dev)
     V = torch.as_tensor(p["V"], dtype=torch.float32, device=dev)
     s = torch.as_tensor(p["sigma"], dtype=torch.float64, device=dev)
     N = p["N"]
-    return SVLCOV(U, s, V, max_m=N + 64, max_n=N + 64, max_s=max_s, max_nnz=max_nnz, storage="fp32", small=small)
+    return SVLCOV(U, s, V, max_m=N + 64, max_n=N + 64, max_s=max_s, max_nnz=max_nnz, storage="fp32", small=small,
+                  jacobi_block=JACOBI_BLOCK)
 
 
 def run_path(p, dev_batches, torch, dev, small, W, K, flush, profile=False, clocks=None):
@@ -736,7 +742,9 @@ def main_stream(args):
 
 
 def main():
+    global JACOBI_BLOCK
     args = parse()
+    JACOBI_BLOCK = args.jacobi_block
     if args.impl == "reference":
         return main_reference(args)
     if args.workload == "c4":
