@@ -265,7 +265,8 @@ def roofline_svd(p, prof, small, sweeps_per_launch, n):
     # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
     peak = 152 * 128 * 2 * 2.07e9 / 1e12
     # DRAM bytes of one k_jacobi_cluster launch at n = 320 (read 773.4 KB: K and G in, all else in shared
-    # memory; write 0), from the ncu capture summarised in profiles/jacobi_cluster_n320_c2.md
+    # memory; write 0), from the ncu capture summarised in profiles/jacobi_cluster_n320_c2.md (same kernel
+    # code; captured with 16-column blocks, the default is now 10: the one-time K and G load is the same)
     traffic = 773376 if n == 320 else None
     svd_ms, svd_calls = prof["svd"]
     return dict(bound="alu", achieved=round(achieved, 4), peak=round(peak, 2), unit="TFLOP/s",
