@@ -79,3 +79,19 @@ def test_autotune_pick_prefers_concurrency_within_slack():
     assert autotune.pick(t2, cands) == (32, 8)          # the 64-lane times are 6% slower
     t3 = {"8x8": 10.0, "8x16": 12.0, "32x8": 20.0, "64x8": 20.0, "64x16": 20.0}
     assert autotune.pick(t3, cands) == (8, 8)
+
+
+def test_roofline_uses_the_sweep_kernels_own_time():
+    """The roofline of the dominant kernel divides its algorithmic flops
+    (9 n^2 (n-1) per sweep) by the sweep kernel's own event-timed duration,
+    not by the whole SVD phase's."""
+    import bench
+    prof = {"svd": (300.0, 100), "jacobi_kernel": (200.0, 100)}   # ms totals, calls
+    r = bench.roofline_svd(None, prof, "mixed", 7.0, 320)
+    flops = 7.0 * 9.0 * 320 * 320 * 319
+    assert r["flops_per_launch"] == flops
+    assert abs(r["ms_per_launch"] - 2.0) < 1e-12
+    assert abs(r["achieved"] - round(flops / 2e-3 / 1e12, 4)) < 1e-4
+    assert abs(r["frac"] - round(r["achieved"] / r["peak"], 5)) < 1e-5
+    assert r["traffic"] == 773376 and r["bound"] == "alu"
+    assert bench.roofline_svd(None, prof, "mixed", 7.0, 640)["traffic"] is None
