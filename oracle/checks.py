@@ -1,4 +1,11 @@
-"""Error measures for comparing truncated SVDs (FP64, numpy)."""
+"""Error measures for comparing truncated SVDs (FP64, numpy).
+
+TEST INFRASTRUCTURE ONLY (part of the oracle): the rulers every parity test
+uses.  Their definitions follow the tolerance reading of the step's result
+(a truncated SVD is compared by its singular values and, across a gap in the
+spectrum, by the principal angles between singular subspaces).  Each is
+pinned against known answers in tests/test_oracle_checks.py.
+"""
 from __future__ import annotations
 
 import numpy as np
@@ -32,12 +39,23 @@ def gapped_prefix(s_ref: np.ndarray, rel_gap: float = 1e-3) -> int:
     return 0
 
 
-def max_sin_angle(X: np.ndarray, Xref: np.ndarray) -> float:
-    """Sine of the largest principal angle between range(X) and range(Xref)."""
+def max_sin_angle(X: np.ndarray, Xref: np.ndarray, rank_tol: float = 1e-10) -> float:
+    """Sine of the largest principal angle between range(X) and range(Xref),
+    two blocks of the same width k'.  The columns need not be orthonormal:
+    both blocks are orthonormalised first (the angles belong to the
+    subspaces).  The sine is the 2-norm of (I - Qr Qr^T) Q.  A block whose
+    columns do not span k' dimensions (a zero or dependent column) has lost a
+    direction, and the angle to it is taken as 90 degrees: 1.0 is returned.
+    An empty block (k' = 0) compares nothing and returns 0."""
+    if X.shape[1] != Xref.shape[1]:
+        raise ValueError("blocks of different width")
     if X.shape[1] == 0:
         return 0.0
-    Q, _ = np.linalg.qr(X)
-    Qr, _ = np.linalg.qr(Xref)
+    Q, R = np.linalg.qr(X)
+    Qr, Rr = np.linalg.qr(Xref)
+    for r in (np.abs(np.diag(R)), np.abs(np.diag(Rr))):
+        if r.min() <= rank_tol * max(r.max(), np.finfo(float).tiny):
+            return 1.0
     res = Q - Qr @ (Qr.T @ Q)
     return float(np.linalg.norm(res, 2))
 
