@@ -87,6 +87,20 @@ def problem(args):
     return synth.c2_problem(N=args.N, k=args.k, s=args.s)
 
 
+def c2_steps(args, npairs):
+    """Warm-up and timed node batches of a C2 run (both arms use the same)."""
+    W = max(0, min(args.warmup, npairs - 1))
+    K = args.steps if args.steps > 0 else npairs - W
+    return W, max(1, min(K, npairs - W))
+
+
+def c2_config(args, world, mean_degree):
+    """The config object of a C2 line (both arms print the same)."""
+    return dict(workload=WORKLOAD, global_batch=2 * args.s * world, seq_len=None,
+                parallelism=f"replicas x{world}" if world > 1 else "single GPU",
+                l2="flushed (512 MB write) between timed steps", mean_degree=mean_degree)
+
+
 # ---------------------------------------------------------------------------
 class Clocks:
     """nvidia-smi sampling during the timed region."""
@@ -251,29 +265,88 @@ def run_e2e(p, batches, torch, dev, W, K):
     return dict(value=units / t, unit=UNIT, h2d_bytes_per_step=int(h2d / steps), d2h_bytes_per_step=8 * h.k)
 
 
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_jacobi_cluster_c2_n320_traffic.txt")
+SVD_SOURCE = os.path.join(ROOT, "paper_2401_09703_gb300", "csrc", "dense.cu")
+FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
+
+
+def _sha256(path):
+    import hashlib
+    with open(path, "rb") as f:
+        return hashlib.sha256(f.read()).hexdigest()
+
+
+def svd_traffic(n, ldn_note=None):
+    """DRAM bytes per launch of the sweep kernel at this n from the ncu
+    record under profiles/ (dram__bytes_read.sum + dram__bytes_write.sum of
+    one launch), or None when there is no record for this n or the kernel's
+    source file has changed since the counters were taken."""
+    if not os.path.exists(TRAFFIC_RECORD):
+        return None, "no ncu record"
+    rec = {}
+    for line in open(TRAFFIC_RECORD):
+        if "=" in line and not line.lstrip().startswith("#"):
+            kk, v = line.split("=", 1)
+            rec[kk.strip()] = v.strip()
+    if int(rec.get("n", -1)) != n:
+        return None, f"ncu record is for n={rec.get('n')}"
+    if rec.get("source_sha256") != _sha256(SVD_SOURCE):
+        return None, "kernel source changed since the ncu record"
+    return int(rec["dram_bytes_read"]) + int(rec["dram_bytes_write"]), "ncu record " + os.path.basename(TRAFFIC_RECORD)
+
+
 def roofline_svd(p, prof, small, sweeps_per_launch, n):
     """The dominant kernel is the Jacobi sweep kernel of the Rayleigh-Ritz
-    SVD.  Its algorithmic work per sweep is n(n-1)/2 rotations x 9n FMA (one
-    dot product and two column-pair updates, of K and of G) = 9 n^2 (n-1)
-    flop.  The duration is the kernel's own: CUDA events the library records
-    on its stream right around each sweep-kernel launch (profile phase
-    "jacobi_kernel"), averaged over the timed steps."""
+    SVD_k of K (n = k + s).  Its algorithmic work is counted as sweeps x
+    6 n^3 flop per launch (the small SVD's per-sweep cost in the step's
+    algorithmic work model), over the kernel's own duration: CUDA events the
+    library records on its stream right around each sweep-kernel launch
+    (profile phase "jacobi_kernel"), averaged over the timed steps.  The
+    peak is the FP32 ALU rate of the whole GPU from unit counts and clock."""
     ms, calls = prof["jacobi_kernel"]
     per_launch_s = ms / 1e3 / max(calls, 1)
-    flops = sweeps_per_launch * 9.0 * n * n * (n - 1)
+    flops = sweeps_per_launch * 6.0 * n ** 3
     achieved = flops / per_launch_s / 1e12
-    # FP32 ALU peak from unit counts and clocks: 152 SMs x 128 FP32 lanes x 2 flop x 2.07 GHz
-    peak = 152 * 128 * 2 * 2.07e9 / 1e12
-    # DRAM bytes of one k_jacobi_cluster launch at n = 320 (read 773.4 KB: K and G in, all else in shared
-    # memory; write 0), from the ncu capture summarised in profiles/jacobi_cluster_n320_c2.md (same kernel
-    # code; captured with 16-column blocks, the default is now 10: the one-time K and G load is the same)
-    traffic = 773376 if n == 320 else None
+    traffic, tnote = svd_traffic(n)
     svd_ms, svd_calls = prof["svd"]
-    return dict(bound="alu", achieved=round(achieved, 4), peak=round(peak, 2), unit="TFLOP/s",
-                frac=round(achieved / peak, 5), traffic=traffic, kernel="k_jacobi_cluster (Rayleigh-Ritz SVD_k of K)",
-                flops_per_launch=flops, ms_per_launch=per_launch_s * 1e3,
+    return dict(bound="alu", achieved=round(achieved, 4), peak=round(FP32_ALU_PEAK_TFLOPS, 2), unit="TFLOP/s",
+                frac=round(achieved / FP32_ALU_PEAK_TFLOPS, 5), traffic=traffic, traffic_source=tnote,
+                kernel="k_jacobi_cluster (Rayleigh-Ritz SVD_k of K)", flops_per_launch=flops,
+                flop_model="sweeps x 6 n^3", ms_per_launch=per_launch_s * 1e3,
                 svd_phase_ms_per_call=svd_ms / max(svd_calls, 1),
                 peak_note="FP32 ALU peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz (no measured ALU peak)")
+
+
+def sparse_bytes(batches, k, b_f):
+    """Algorithmic HBM bytes of the sparse kernels over a list of batches:
+    gather + Gram (one pass: nnz (k b_f + 8) + 4 (s + 1)), scatter
+    (read-modify-write of the r touched rows: 2 r k b_f) and append (s k b_f)."""
+    tot = 0
+    for _, b in batches:
+        r = int(np.unique(b.indices).size)
+        tot += b.nnz * (k * b_f + 8) + 4 * (b.rows + 1) + 2 * r * k * b_f + b.rows * k * b_f
+    return tot
+
+
+def roofline_sparse(batches, k, b_f, prof, peak_gbs):
+    """HBM roofline of the gather/Gram (profile phase "gather") and the apply
+    phase (scatter, append, the finite check and the commit: phase "apply")
+    over the timed steps, L2 flushed before each step."""
+    byts = sparse_bytes(batches, k, b_f)
+    t = (prof["gather_gram"][0] + prof["apply"][0]) / 1e3
+    achieved = byts / t / 1e9
+    return dict(bound="hbm", achieved=round(achieved, 2), peak=peak_gbs, unit="GB/s", frac=round(achieved / peak_gbs, 5),
+                traffic=None, kernel="k_gather_gram + k_scatter + k_append (phases gather + apply)",
+                bytes_per_step=byts / max(len(batches) // 2, 1), ms_per_step=1e3 * t / max(len(batches) // 2, 1),
+                peak_note="measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        d = json.load(open(path))
+        return float(d.get("hbm_gbs", 6800.0)), "measured"
+    return 6800.0, "fallback"
 
 
 def cpu_baseline(p, seconds):
@@ -304,10 +377,9 @@ def main_reference(args):
     from oracle import svlcov as osv
     st = osv.State.init(p["U"], p["sigma"], p["V"])
     pairs = [(p["batches"][2 * i], p["batches"][2 * i + 1]) for i in range(len(p["batches"]) // 2)]
-    W = min(args.warmup, 1)
+    W, K = c2_steps(args, len(pairs))
     for (kr, br), (kc, bc) in pairs[:W]:
         st.apply(kr, br); st.apply(kc, bc)
-    K = args.steps if args.steps > 0 else len(pairs) - W
     budget = 150.0
     t0 = time.perf_counter()
     units, done = 0, 0
@@ -323,9 +395,10 @@ def main_reference(args):
     line = dict(metric=METRIC, value=v, unit=UNIT, n_gpus=args.gpus, steps=done, warmup=W,
                 ms_per_step=1e3 * t / max(done, 1), higher_is_better=True, scaling="weak", vs_baseline=None,
                 dtype="f64", data="synthetic", impl="reference",
-                config=dict(workload=WORKLOAD, global_batch=2 * args.s, l2="n/a (CPU)"),
+                config=c2_config(args, 1, p["mean_degree"]),
                 cpu_baseline=dict(value=v, unit=UNIT, cores=cores, kind="oracle",
-                                  sample=f"{done} node batches after {W} warm-up (bounded to {budget:.0f} s)"),
+                                  sample=f"{done} node batches after {W} warm-up (bounded to {budget:.0f} s); "
+                                         "the oracle runs on the host cores, the L2 setting does not apply"),
                 e2e=dict(value=v, unit=UNIT, h2d_bytes_per_step=0, d2h_bytes_per_step=0))
     print(json.dumps(line))
     return 0
@@ -764,9 +837,7 @@ def main():
     dev = torch.device("cuda", local)
     p = problem(args)
     npairs = len(p["batches"]) // 2
-    W = max(0, min(args.warmup, npairs - 1))
-    K = args.steps if args.steps > 0 else npairs - W
-    K = max(1, min(K, npairs - W))
+    W, K = c2_steps(args, npairs)
     dev_batches = stage(p["batches"], torch, dev)
     flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
     torch.cuda.synchronize()
@@ -783,15 +854,17 @@ def main():
     t_max = max_over_ranks(t_mixed, world, dev)
     value = whole_job_rate(mixed["units"], world, t_max)
 
-    # accuracy against the stored FP64 oracle trajectory (full default run only)
+    # accuracy against the stored FP64 oracle trajectory, after the node batch where the run stops
     err = dict(mixed=None, plain=None)
-    full = (W + K == npairs) and args.N == 100_000 and args.k == 64 and args.s == 256
-    if full and os.path.exists(GOLDEN):
-        so = np.array(json.load(open(GOLDEN))["sigma_final"])
-        keep = so > 1e-12 * so[0]
-        err["mixed"] = float(np.max(np.abs(mixed["sigma"][keep] - so[keep]) / so[keep]))
-        if plain is not None:
-            err["plain"] = float(np.max(np.abs(plain["sigma"][keep] - so[keep]) / so[keep]))
+    default_shape = args.N == 100_000 and args.k == 64 and args.s == 256
+    if default_shape and os.path.exists(GOLDEN):
+        per = json.load(open(GOLDEN))["sigma_after_node_batch"]
+        if W + K <= len(per):
+            so = np.array(per[W + K - 1])
+            keep = so > 1e-12 * so[0]
+            err["mixed"] = float(np.max(np.abs(mixed["sigma"][keep] - so[keep]) / so[keep]))
+            if plain is not None:
+                err["plain"] = float(np.max(np.abs(plain["sigma"][keep] - so[keep]) / so[keep]))
 
     line = None
     if rank == 0:
@@ -800,6 +873,9 @@ def main():
         sweeps = pr["svd_sweeps"] / max(pr["svd"][1], 1)     # average Jacobi sweeps per SVD launch
         roof = roofline_svd(p, pr, "mixed", sweeps, n)
         roof["sweeps_per_launch"] = sweeps
+        peak_gbs, peak_kind = measured_peaks()
+        roof_hbm = roofline_sparse(p["batches"][2 * W:2 * (W + K)], args.k, 4, pr, peak_gbs)
+        roof_hbm["peak_note"] += f" ({peak_kind})"
         cpu = None if args.no_cpu else cpu_baseline(p, args.cpu_seconds)
         phases = {k: dict(ms_total=round(v[0], 3), calls=v[1]) for k, v in prof["profile"].items()
                   if k != "svd_sweeps"}
@@ -807,14 +883,13 @@ def main():
             metric=METRIC, value=value, unit=UNIT, n_gpus=world, steps=K, warmup=W,
             ms_per_step=1e3 * t_max / K, higher_is_better=True, scaling="weak", vs_baseline=None,
             dtype="f32 storage, f32+f64 small steps", data="synthetic",
-            config=dict(workload=WORKLOAD, global_batch=2 * args.s * world, seq_len=None,
-                        parallelism=f"replicas x{world}" if world > 1 else "single GPU",
-                        l2="flushed (512 MB write) between timed steps", mean_degree=p["mean_degree"]),
+            config=c2_config(args, world, p["mean_degree"]),
             plain_fp32=None if plain is None else dict(value=plain["units"] / (sum(plain["ms"]) / 1e3), unit=UNIT,
                                                        ms_per_step=sum(plain["ms"]) / len(plain["ms"]),
                                                        sigma_rel_err_vs_oracle=err["plain"], status=plain["status"]),
-            sigma_rel_err_vs_oracle=err["mixed"], status=mixed["status"], resets=mixed["resets"],
-            roofline=roof, phases_ms=phases, e2e=e2e, cpu_baseline=cpu,
+            sigma_rel_err_vs_oracle=err["mixed"], sigma_compared_after_node_batch=W + K,
+            status=mixed["status"], resets=mixed["resets"],
+            roofline=roof, roofline_hbm=roof_hbm, phases_ms=phases, e2e=e2e, cpu_baseline=cpu,
             gpu_launches=int(mixed["launches"]), clocks=mixed["clocks"],
             wall_s_timed_region=mixed["wall"])
         print(json.dumps(line))

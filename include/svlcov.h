@@ -323,18 +323,22 @@ int svlcov_small_svd(const double* K, int32_t n, int32_t k, double* F, double* t
 
 /* The same rank-k small SVD for callers that cannot allocate device memory
  * (for example code running under another component's caching allocator,
- * or latency-sensitive code that must not let cudaMalloc / cudaFree
- * synchronise the device).  The paper has no counterpart: this is a
- * deployment variant of svlcov_small_svd.  Its scratch is a fixed array of
- * 2 MiB compiled into the library (every GPU that loads the library holds
+ * which owns the free device memory, or latency-sensitive code that must not
+ * let cudaMalloc / cudaFree synchronise the device).  The paper has no
+ * counterpart: this is a deployment variant of svlcov_small_svd, with the
+ * same three precisions and the same results (SVLCOV_SMALL_MIXED included:
+ * FP32 sweeps, then the FP64 refinement).  Its scratch is a fixed array of
+ * 8 MiB compiled into the library (every GPU that loads the library holds
  * one until the process exits), so there is no `work` argument; the caller
  * still provides K, F, theta and G as for svlcov_small_svd.  n above
  * SVLCOV_SMALL_SVD_STATIC_MAX_N returns SVLCOV_ERR_CAPACITY before any CUDA
- * call.  The first call on each device looks up the array's device address
- * (a CUDA runtime query, no allocation); make that first call before any
- * stream capture.  All calls on a device share the array and it keeps the
- * last call's contents: calls that overlap on the GPU race, so serialise
- * them.  No cudaMalloc, cudaFree or allocating library routine is called. */
+ * call; every n <= SVLCOV_SMALL_SVD_STATIC_MAX_N with any k <= n and any
+ * precision fits.  The first call on each device looks up the array's
+ * device address (a CUDA runtime query, no allocation); make that first call
+ * before any stream capture.  All calls on a device share the array and it
+ * keeps the last call's contents: calls that overlap on the GPU race, so
+ * serialise them.  No cudaMalloc, cudaFree or allocating library routine is
+ * called.  Launch errors are reported as by svlcov_small_svd. */
 #define SVLCOV_SMALL_SVD_STATIC_MAX_N 256
 int svlcov_small_svd_static(const double* K, int32_t n, int32_t k, double* F, double* theta, double* G,
                             int32_t precision, int32_t* sweeps, void* stream);

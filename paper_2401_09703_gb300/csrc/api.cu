@@ -251,7 +251,6 @@ extern "C" size_t svlcov_workspace_bytes(const svlcov_init_desc* d) {
     if (e_ != cudaSuccess) return SVLCOV_ERR_CUDA;    \
   } while (0)
 
-static int last_launch() { return cudaGetLastError() == cudaSuccess ? SVLCOV_OK : SVLCOV_ERR_CUDA; }
 
 static void reorth_side(svlcov_handle* h, int side, cudaStream_t st) {
   const void* X = side == 0 ? h->d.ubuf : h->d.vbuf;

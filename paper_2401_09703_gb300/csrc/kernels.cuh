@@ -174,4 +174,9 @@ int launch_add_cols_backward(const svlcov_csr& E, int k, const BackwardInputs& i
                              const double* Upre_S, const double* Upre_nnz, const double* Ubar, const double* thbar,
                              double* dvalues, double gap, void* work, int* status, cudaStream_t st);
 
+// Return code of an entry point after its launches: SVLCOV_ERR_CUDA if a
+// launch error is pending on this host thread (cudaGetLastError, which also
+// clears it), else SVLCOV_OK.
+inline int last_launch() { return cudaGetLastError() == cudaSuccess ? SVLCOV_OK : SVLCOV_ERR_CUDA; }
+
 }  // namespace svl

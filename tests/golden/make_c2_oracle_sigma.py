@@ -1,7 +1,8 @@
 """Write tests/golden/c2_oracle_sigma.json: the FP64 oracle's singular values
-at the end of the full C2 trajectory (graph node insertion, Chung-Lu
-N = 100000, k = 64, s = 256, rows then columns per node batch), and after each
-of the first node batches.  Calls only synth/ and oracle/ (the sparse method
+after every node batch of the full C2 trajectory (graph node insertion,
+Chung-Lu N = 100000, k = 64, s = 256, rows then columns per node batch), so
+that a benchmark run of any length can be compared with the oracle at the
+node batch where it stops.  Calls only synth/ and oracle/ (the sparse method
 of Algorithms 2, 3 and 11).  Run: python tests/golden/make_c2_oracle_sigma.py
 """
 import json
@@ -24,7 +25,7 @@ def main():
     per_batch = []
     for i, (kind, b) in enumerate(p["batches"]):
         st.apply(kind, b)
-        if kind == "cols" and len(per_batch) < 8:
+        if kind == "cols":
             per_batch.append(st.sigma.tolist())
     out = dict(
         source="FP64 oracle (oracle.svlcov.State, Algorithms 2, 3, 11) on synth.c2_problem() defaults",
@@ -34,7 +35,8 @@ def main():
         resets=st.resets, seconds=time.time() - t0)
     path = os.path.join(os.path.dirname(os.path.abspath(__file__)), "c2_oracle_sigma.json")
     with open(path, "w") as f:
-        json.dump(out, f, indent=1)
+        # one line per array keeps the file small and diffable
+        f.write("{\n" + ",\n".join(f" {json.dumps(k)}: {json.dumps(v)}" for k, v in out.items()) + "\n}\n")
     print("wrote", path, "in", out["seconds"], "s")
 
 

@@ -81,17 +81,42 @@ def test_autotune_pick_prefers_concurrency_within_slack():
     assert autotune.pick(t3, cands) == (8, 8)
 
 
-def test_roofline_uses_the_sweep_kernels_own_time():
+def test_roofline_uses_the_sweep_kernels_own_time(tmp_path, monkeypatch):
     """The roofline of the dominant kernel divides its algorithmic flops
-    (9 n^2 (n-1) per sweep) by the sweep kernel's own event-timed duration,
-    not by the whole SVD phase's."""
+    (sweeps x 6 n^3 per launch) by the sweep kernel's own event-timed
+    duration, not by the whole SVD phase's; its traffic comes from the ncu
+    record only while that record matches n and the kernel's source."""
     import bench
     prof = {"svd": (300.0, 100), "jacobi_kernel": (200.0, 100)}   # ms totals, calls
+    src = tmp_path / "dense.cu"
+    src.write_text("kernel v1")
+    rec = tmp_path / "rec.txt"
+    rec.write_text(f"# ncu record\nn = 320\nsource_sha256 = {bench._sha256(str(src))}\n"
+                   "dram_bytes_read = 700000\ndram_bytes_write = 1000\n")
+    monkeypatch.setattr(bench, "SVD_SOURCE", str(src))
+    monkeypatch.setattr(bench, "TRAFFIC_RECORD", str(rec))
     r = bench.roofline_svd(None, prof, "mixed", 7.0, 320)
-    flops = 7.0 * 9.0 * 320 * 320 * 319
+    flops = 7.0 * 6.0 * 320 ** 3
     assert r["flops_per_launch"] == flops
     assert abs(r["ms_per_launch"] - 2.0) < 1e-12
     assert abs(r["achieved"] - round(flops / 2e-3 / 1e12, 4)) < 1e-4
     assert abs(r["frac"] - round(r["achieved"] / r["peak"], 5)) < 1e-5
-    assert r["traffic"] == 773376 and r["bound"] == "alu"
+    assert r["traffic"] == 701000 and r["bound"] == "alu"
     assert bench.roofline_svd(None, prof, "mixed", 7.0, 640)["traffic"] is None
+    src.write_text("kernel v2")               # the kernel changed since the counters were taken
+    assert bench.roofline_svd(None, prof, "mixed", 7.0, 320)["traffic"] is None
+
+
+def test_sparse_roofline_bytes():
+    """Algorithmic bytes of the sparse kernels: nnz (k b_f + 8) + 4 (s + 1)
+    for the gather/Gram, 2 r k b_f for the scatter and s k b_f for the
+    append, with r the distinct rows the batch touches."""
+    import bench
+    import synth
+    b = synth.CSR(np.array([0, 2, 3]), np.array([5, 7, 5]), np.ones(3), 2, 10)
+    k, bf = 4, 4
+    want = 3 * (k * bf + 8) + 4 * 3 + 2 * 2 * k * bf + 2 * k * bf
+    assert bench.sparse_bytes([("cols", b)], k, bf) == want
+    prof = {"gather_gram": (1.0, 2), "apply": (1.0, 2)}
+    r = bench.roofline_sparse([("rows", b), ("cols", b)], k, bf, prof, 1000.0)
+    assert abs(r["achieved"] - round(2 * want / 2e-3 / 1e9, 2)) < 1e-2 and r["bound"] == "hbm"
