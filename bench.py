@@ -270,10 +270,19 @@ SVD_SOURCE = os.path.join(ROOT, "paper_2401_09703_gb300", "csrc", "dense.cu")
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 
 
-def _sha256(path):
+SVD_MARKERS = ("// ==== Jacobi sweep kernels: begin ====", "// ==== Jacobi sweep kernels: end ====")
+
+
+def _sha256(path, markers=SVD_MARKERS):
+    """sha256 of the source text strictly between the two marker lines (the
+    sweep kernel and the device functions it calls), or of the whole file
+    when the markers are absent."""
     import hashlib
-    with open(path, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()
+    text = open(path, encoding="utf-8").read()
+    a, b = text.find(markers[0]), text.find(markers[1])
+    if a >= 0 and b > a:
+        text = text[text.index("\n", a) + 1:b]
+    return hashlib.sha256(text.encode("utf-8")).hexdigest()
 
 
 def svd_traffic(n, ldn_note=None):

@@ -115,6 +115,11 @@ typedef struct {
                           /*   side by side, e.g. in svlcov_batch_run, where   */
                           /*   the GPU is full anyway).  Results depend on it  */
                           /*   (summation order), not on how a step is run.    */
+  int32_t tensor_gemm;    /* SVLCOV_SMALL_MIXED: its FP64 small products (folds,*/
+                          /*   C0, CholeskyQR2 Gram, SVD refinement) run on the */
+                          /*   tensor cores as exact BF16 digit products       */
+                          /*   (Ozaki splitting, see svlcov_dgemm): 0 default  */
+                          /*   (on), < 0 on the FP64 pipe.  Other modes: unused */
 } svlcov_init_desc;
 
 /* One item of a batched run: kind 0 = add columns (a), 1 = add rows (a),
@@ -307,6 +312,25 @@ void svlcov_destroy(svlcov_handle* h);
 const char* svlcov_strerror(int32_t code);
 
 /* ---- standalone dense kernels (same code as inside a step) -------------- */
+
+/* C (M x N) = alpha op(A) op(B) + beta C in FP64, column-major (op = the
+ * matrix or its transpose, ta / tb nonzero for the transpose; lda, ldb, ldc
+ * leading dimensions), all pointers device memory; the small dense products
+ * of a step (Section 3.2 folds, C0 = W^T P, CholeskyQR2, Rayleigh-Ritz
+ * refinement).  engine 0: the FP64 pipe (tiled SIMT, split K over a
+ * cluster for small products); engine 1: the tensor cores -- every row of
+ * op(A) and column of op(B) is written on the grid of its largest exponent
+ * and cut into seven 7-bit digits (Ozaki splitting), each digit pair's
+ * product is accumulated exactly by BF16 tcgen05.mma in FP32 tensor memory,
+ * and the products are summed in FP64; accurate to ~2^-49 of
+ * max_k |a_ik| max_k |b_kj| per term (FP64 GEMM accuracy for a few hundred
+ * terms), subnormal inputs read as zero, a non-finite input gives NaN in its
+ * row / column.  M, N, K <= 4096.  Asynchronous on `stream`; returns
+ * SVLCOV_ERR_INVALID_ARG for bad sizes or pointers, SVLCOV_ERR_CUDA for a
+ * launch error. */
+int svlcov_dgemm(int32_t ta, int32_t tb, int32_t M, int32_t N, int32_t K, double alpha, const double* A,
+                 int32_t lda, const double* B, int32_t ldb, double beta, double* C, int32_t ldc, int32_t engine,
+                 void* stream);
 
 /* Rank-k SVD of a small dense matrix (the Rayleigh-Ritz step of Section 2.1,
  * SVD_k of K): one-sided Jacobi.  K: device, n x n column-major FP64 (not

@@ -135,9 +135,18 @@ struct svlcov_handle {
 
 // The handle's split-K setting for the FP64 products it enqueues (restored
 // on leaving the entry point).
+// The same scope sets where the handle's FP64 products run: on the tensor
+// cores (ozaki_gemm) for the mixed small-step mode unless the handle's
+// tensor_gemm option is negative, else on the FP64 pipe.
 struct SplitScope {
-  explicit SplitScope(const svlcov_handle* h) { set_gemm_split(!h || h->d.gemm_split >= 0); }
-  ~SplitScope() { set_gemm_split(true); }
+  explicit SplitScope(const svlcov_handle* h) {
+    set_gemm_split(!h || h->d.gemm_split >= 0);
+    set_gemm_tc(h && h->d.small == SVLCOV_SMALL_MIXED && h->d.tensor_gemm >= 0);
+  }
+  ~SplitScope() {
+    set_gemm_split(true);
+    set_gemm_tc(false);
+  }
 };
 
 // Re-orthonormalisation of the projected factor(s) before a step (see the
@@ -462,6 +471,24 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
     gemm<TC>(false, false, s, s, s, (TC)1, Y1, s, T1, s, (TC)0, S2, s, status, st, TRI_A_LO);  // S2 = Y1 S Y1^T
     launch_cholinv<float, double, true>((double*)S2, s, nullptr, (float)h->d.tau, (double*)L2, (double*)Y2,
                                         sb.defl2, (double*)S, (double*)T1, status, st);
+    // X = Y1^T Y2^T is R^-1 to ~eps32^2 cond(S), but R2 R1 = L2^T L1^T is not
+    // its inverse: Y1 is an FP32 inverse of L1, off by ~eps32 cond(S), and
+    // that error would enter K.  The R consistent with the X the folds use is
+    // R = Q^T (E - U C0) = X^T S (upper triangular up to ~eps32^2 cond(S)),
+    // from S formed again (pass 2 clobbered it; its Gram in S2 is no longer
+    // needed) in FP64.
+    {
+      SideFork fk(h, st);
+      gemm<TC>(true, true, s, s, s, (TC)1, Y1, s, Y2, s, (TC)0, X, s, status, fk.stream(),
+               TRI_A_UP | TRI_B_UP);                                                                    // X = Y1^T Y2^T
+      launch_copy<TC>((TC*)sb.SE, S2, (int64_t)s * s, status, st);
+      gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S2, s, status, st);          // S = S_E - C0^T C0
+    }
+    gemm<TC>(true, false, s, s, s, (TC)1, X, s, S2, s, (TC)0, R, s, status, st, TRI_A_LO);          // R = X^T S
+    launch_triu((double*)R, s, status, st);
+    gemm<TC>(false, false, k, s, s, (TC)1, C0, k, X, s, (TC)0, CQ, k, status, st, TRI_B_UP);       // C_Q = C0 X
+    h->prof.end(st);
+    return;
   } else {
     launch_cholinv<TC, TC, false>(S, s, e2, tau, L1, Y1, sb.defl1, S2, T1, status, st);         // S = L1 L1^T, Y1 = L1^-1
     gemm<TC>(false, true, s, s, s, (TC)1, S, s, Y1, s, (TC)0, T1, s, status, st, TRI_B_UP);   // T1 = S Y1^T
@@ -1306,6 +1333,21 @@ extern "C" const char* svlcov_strerror(int32_t code) {
     case SVLCOV_DEV_TIMEOUT: return "bounded device wait expired";
     default: return "combination of device status bits";
   }
+}
+
+// ---- standalone dense product --------------------------------------------------
+extern "C" int svlcov_dgemm(int32_t ta, int32_t tb, int32_t M, int32_t N, int32_t K, double alpha, const double* A,
+                            int32_t lda, const double* B, int32_t ldb, double beta, double* C, int32_t ldc,
+                            int32_t engine, void* stream) {
+  if (M < 0 || N < 0 || K < 0 || M > 4096 || N > 4096 || K > 4096 || (engine != 0 && engine != 1))
+    return SVLCOV_ERR_INVALID_ARG;
+  if (M == 0 || N == 0) return SVLCOV_OK;
+  if (!C || ldc < M || (K > 0 && (!A || !B))) return SVLCOV_ERR_INVALID_ARG;
+  if (K > 0 && (lda < (ta ? K : M) || ldb < (tb ? N : K))) return SVLCOV_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  GemmTcScope tc(engine == 1);
+  gemm<double>(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, st);
+  return last_launch();
 }
 
 // ---- standalone small SVD ----------------------------------------------------

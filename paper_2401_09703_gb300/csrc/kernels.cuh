@@ -61,6 +61,20 @@ template <typename T>
 void gemm(bool ta, bool tb, int M, int N, int Kd, T alpha, const T* A, int lda, const T* B, int ldb,
           T beta, T* C, int ldc, const int* status, cudaStream_t st, int tri = 0);
 enum { TRI_A_UP = 1, TRI_A_LO = 2, TRI_B_UP = 4, TRI_B_LO = 8 };
+// The same FP64 product on the tensor cores: operands split into 7-bit BF16
+// digits (Ozaki), exact digit-pair products accumulated in FP32 tensor
+// memory by tcgen05.mma, summed in FP64 (csrc/tcgemm.cu).
+void ozaki_gemm(bool ta, bool tb, int M, int N, int Kd, double alpha, const double* A, int lda, const double* B,
+                int ldb, double beta, double* C, int ldc, const int* status, cudaStream_t st, int tri = 0);
+// Whether this host thread's FP64 gemm() calls run as ozaki_gemm (set for the
+// steps of mixed-mode handles whose tensor_gemm option is on).
+void set_gemm_tc(bool on);
+bool gemm_tc();
+struct GemmTcScope {
+  bool prev;
+  explicit GemmTcScope(bool on) : prev(gemm_tc()) { set_gemm_tc(on); }
+  ~GemmTcScope() { set_gemm_tc(prev); }
+};
 size_t cholinv_smem_bytes(int s, size_t elem);
 // Cholesky with deflation S = L L^T and Y = L^-1 (dropped rows and columns
 // zeroed), factor arithmetic in T on SrcT data: one CTA in shared memory when
@@ -114,6 +128,7 @@ void launch_inverse(const T* W, int k, T* Winv, double thr, int* do_reset, int* 
                     T* tmp = nullptr);
 template <typename T>
 void launch_copy(const T* src, T* dst, int64_t count, const int* status, cudaStream_t st);
+void launch_triu(double* A, int n, const int* status, cudaStream_t st);
 template <typename T>
 void launch_commit(T* Wu, const T* Wu_new, const int* reset_u, T* Wv, const T* Wv_new, const int* reset_v,
                    T* sigma, const T* theta, int k, int64_t* counters, int64_t dm, int64_t dn,

@@ -65,7 +65,7 @@ class SVLCOV:
     def __init__(self, U0: torch.Tensor, sigma0: torch.Tensor, V0: torch.Tensor, *, max_m: int, max_n: int,
                  max_s: int, max_nnz: int, storage: str = "fp32", small: str = "mixed", tau: float = 0.0,
                  reset_threshold: float = 0.0, jacobi_block: int = 0, reorth: int = 0, gemm_split: int = 0,
-                 stream=None):
+                 tensor_gemm: int = 0, stream=None):
         assert U0.is_cuda and V0.is_cuda and sigma0.is_cuda
         m, k = U0.shape
         n = V0.shape[0]
@@ -89,6 +89,7 @@ class SVLCOV:
         d.jacobi_block = jacobi_block
         d.reorth = reorth
         d.gemm_split = gemm_split
+        d.tensor_gemm = tensor_gemm
         nbytes = lib().svlcov_workspace_bytes(C.byref(d))
         if nbytes == 0:
             raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_workspace_bytes")
@@ -328,6 +329,27 @@ def batch_run(items, concurrency: int = 16, stream=None):
 
 def kernel_launches() -> int:
     return int(lib().svlcov_kernel_launches())
+
+
+def dgemm(A: torch.Tensor, B: torch.Tensor, *, ta: bool = False, tb: bool = False, alpha: float = 1.0,
+          beta: float = 0.0, C: torch.Tensor = None, engine: str = "tensor", stream=None) -> torch.Tensor:
+    """alpha op(A) op(B) + beta C in FP64 with the library's product kernels
+    (engine "tensor": BF16 digit products on the tensor cores; "fp64": the
+    FP64 pipe).  Tensors are device FP64 matrices in the usual row-major
+    torch layout; they are handed to the column-major C call as transposes."""
+    A = A.to(torch.float64).contiguous()
+    B = B.to(torch.float64).contiguous()
+    M = A.shape[1] if ta else A.shape[0]
+    K = A.shape[0] if ta else A.shape[1]
+    N = B.shape[0] if tb else B.shape[1]
+    if C is None:
+        C = torch.zeros((M, N), dtype=torch.float64, device=A.device)
+    Ct = C.t().contiguous()                       # column-major M x N
+    # row-major A (r x c) is column-major A^T: op(A) = A means the transpose flag set on the column-major view
+    check(lib().svlcov_dgemm(0 if ta else 1, 0 if tb else 1, M, N, K, alpha, _ptr(A), A.shape[1], _ptr(B),
+                             B.shape[1], beta, _ptr(Ct), M, {"fp64": 0, "tensor": 1}[engine], _stream(stream)),
+          "svlcov_dgemm")
+    return Ct.t()
 
 
 def small_svd(K: torch.Tensor, k: int, precision: str = "fp64", stream=None):

@@ -89,7 +89,8 @@ def test_roofline_uses_the_sweep_kernels_own_time(tmp_path, monkeypatch):
     import bench
     prof = {"svd": (300.0, 100), "jacobi_kernel": (200.0, 100)}   # ms totals, calls
     src = tmp_path / "dense.cu"
-    src.write_text("kernel v1")
+    mk = bench.SVD_MARKERS
+    src.write_text(f"other code\n{mk[0]}\nkernel v1\n{mk[1]}\nmore")
     rec = tmp_path / "rec.txt"
     rec.write_text(f"# ncu record\nn = 320\nsource_sha256 = {bench._sha256(str(src))}\n"
                    "dram_bytes_read = 700000\ndram_bytes_write = 1000\n")
@@ -103,7 +104,9 @@ def test_roofline_uses_the_sweep_kernels_own_time(tmp_path, monkeypatch):
     assert abs(r["frac"] - round(r["achieved"] / r["peak"], 5)) < 1e-5
     assert r["traffic"] == 701000 and r["bound"] == "alu"
     assert bench.roofline_svd(None, prof, "mixed", 7.0, 640)["traffic"] is None
-    src.write_text("kernel v2")               # the kernel changed since the counters were taken
+    src.write_text(f"changed elsewhere\n{mk[0]}\nkernel v1\n{mk[1]}\nmore")   # outside the kernel: kept
+    assert bench.roofline_svd(None, prof, "mixed", 7.0, 320)["traffic"] == 701000
+    src.write_text(f"other code\n{mk[0]}\nkernel v2\n{mk[1]}\nmore")   # the kernel changed since the counters
     assert bench.roofline_svd(None, prof, "mixed", 7.0, 320)["traffic"] is None
 
 
