@@ -320,12 +320,12 @@ const char* svlcov_strerror(int32_t code);
  * refinement).  engine 0: the FP64 pipe (tiled SIMT, split K over a
  * cluster for small products); engine 1: the tensor cores -- every row of
  * op(A) and column of op(B) is written on the grid of its largest exponent
- * and cut into seven 7-bit digits (Ozaki splitting), each digit pair's
- * product is accumulated exactly by BF16 tcgen05.mma in FP32 tensor memory,
- * and the products are summed in FP64; accurate to ~2^-49 of
- * max_k |a_ik| max_k |b_kj| per term (FP64 GEMM accuracy for a few hundred
- * terms), subnormal inputs read as zero, a non-finite input gives NaN in its
- * row / column.  M, N, K <= 4096.  Asynchronous on `stream`; returns
+ * and cut into eight 7-bit digits (Ozaki splitting, exact), the products of
+ * the digit pairs with s + t < 8 are accumulated exactly by BF16
+ * tcgen05.mma in FP32 tensor memory, and the groups are summed in FP64;
+ * accurate to ~2^-52 of max_k |a_ik| max_k |b_kj| per term (FP64 GEMM
+ * accuracy), subnormal inputs read as zero, a non-finite input gives NaN in
+ * its row / column.  M, N, K <= 4096.  Asynchronous on `stream`; returns
  * SVLCOV_ERR_INVALID_ARG for bad sizes or pointers, SVLCOV_ERR_CUDA for a
  * launch error. */
 int svlcov_dgemm(int32_t ta, int32_t tb, int32_t M, int32_t N, int32_t K, double alpha, const double* A,

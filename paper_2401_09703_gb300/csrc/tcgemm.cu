@@ -8,16 +8,16 @@
 // its applications", Numer. Algorithms 59, 2012): every row i of op(A) is
 // written on the grid of its largest exponent E_i, a_ik = +-q_ik 2^(E_i-1075)
 // with q_ik < 2^53 the significand shifted right by E_i - e(a_ik), and q_ik
-// is cut into S digits of 7 bits, q = sum_s d_s 2^(46 - 7 s) (the lowest 4
-// bits dropped: 2^-49 of the row's largest element).  Columns of op(B) the
-// same with their own F_j.  Each digit is an integer of magnitude <= 127,
+// is cut into S = 8 digits of 7 bits, q = sum_s d_s 2^(46 - 7 s) (the last
+// digit holds the lowest 4 bits, shifted left by 3: q is represented
+// exactly).  Columns of op(B) the same with their own F_j.  Each digit is an integer of magnitude <= 127,
 // exact in BF16, each digit product exact in FP32, and a sum of at most 1024
 // of them stays below 2^24: so the tensor cores accumulate the partial
 // product of every digit pair without rounding, in any order.  Pairs with
 // the same s + t = g share the scale 2^(92 - 7 g + E_i + F_j - 2150) and one
-// FP32 accumulator in tensor memory; pairs with s + t >= S are dropped
-// (below 2^-49 relative to the row and column scales, the accuracy of an
-// FP64 product of a few hundred terms).  The epilogue turns the S exact
+// FP32 accumulator in tensor memory (8 groups x 64 columns fill the 512
+// columns); pairs with s + t >= 8 are dropped (together below 2^-53 of the
+// product of the row and column scales per term).  The epilogue turns the S exact
 // integer accumulators into FP64 and sums them, smallest first.
 //
 // One CTA computes a 128 x 64 tile of C over a share of K (<= 1024).  Small
@@ -37,7 +37,7 @@ namespace svl {
 
 namespace {
 
-constexpr int OZ_S = 7;        // digits per element
+constexpr int OZ_S = 8;        // digits per element; also the number of accumulator groups
 constexpr int OZ_TM = 128;     // MMA M: rows of op(A) per CTA (tensor-memory lanes)
 constexpr int OZ_TN = 64;      // MMA N: columns of op(B) per CTA
 constexpr int OZ_KC = 64;      // K per shared-memory fill (4 MMAs of K = 16)
@@ -123,7 +123,7 @@ __device__ __forceinline__ uint64_t elem_bits(const double* X, int ld, bool tran
   return (uint64_t)__double_as_longlong(v);
 }
 
-// The seven 7-bit digits of one element on the grid of exponent emax, as
+// The eight 7-bit digits of one element on the grid of exponent emax, as
 // signed BF16 bit patterns (an integer d <= 127 has at most 7 significant
 // bits, so its FP32 pattern shifted right by 16 is its exact BF16).
 __device__ __forceinline__ void digits(uint64_t u, int emax, uint16_t* d) {
@@ -137,7 +137,7 @@ __device__ __forceinline__ void digits(uint64_t u, int emax, uint16_t* d) {
   const uint16_t sg = (uint16_t)((u >> 63) << 15);
 #pragma unroll
   for (int s = 0; s < OZ_S; ++s) {
-    const uint32_t di = (uint32_t)(q >> (46 - 7 * s)) & 127u;
+    const uint32_t di = (uint32_t)(s < 7 ? (q >> (46 - 7 * s)) : (q << 3)) & 127u;
     d[s] = (uint16_t)(__float_as_uint((float)di) >> 16) | (di ? sg : (uint16_t)0);
   }
 }

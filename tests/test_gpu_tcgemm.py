@@ -2,10 +2,11 @@
 digit splitting, exact BF16 digit products in FP32 tensor memory) against
 numpy's FP64 product and the FP64-pipe engine, through the C ABI.
 
-Bound: the digit representation keeps every element to 2^-49 of its row's
-(column's) largest magnitude and the dropped digit pairs are below the same
-scale, so |C_tc - AB| <= c K 2^-49 max|a_i.| max|b_.j| beside the FP64
-rounding K eps |A||B| of the reference itself."""
+Bound: the eight digits represent every element exactly on the grid of its
+row's (column's) largest exponent, and the dropped digit pairs (s + t >= 8)
+stay below 2^-53 of the product of the two scales per term, so
+|C_tc - AB| <= c K 2^-52 max|a_i.| max|b_.j| beside the FP64 rounding
+K eps |A||B| of the reference itself (c = 4)."""
 import numpy as np
 import pytest
 
@@ -27,7 +28,7 @@ def _bound(a, b):
     K = a.shape[1]
     rm = np.abs(a).max(axis=1)[:, None]
     cm = np.abs(b).max(axis=0)[None, :]
-    return 8 * K * 2.0 ** -49 * rm * cm + 2 * K * EPS * (np.abs(a) @ np.abs(b))
+    return 4 * K * 2.0 ** -52 * rm * cm + 2 * K * EPS * (np.abs(a) @ np.abs(b))
 
 
 SHAPES = [(1, 1, 1), (7, 5, 3), (64, 64, 64), (320, 72, 320), (256, 256, 256), (200, 130, 1100),
