@@ -115,11 +115,20 @@ typedef struct {
                           /*   side by side, e.g. in svlcov_batch_run, where   */
                           /*   the GPU is full anyway).  Results depend on it  */
                           /*   (summation order), not on how a step is run.    */
-  int32_t tensor_gemm;    /* SVLCOV_SMALL_MIXED: its FP64 small products (folds,*/
-                          /*   C0, CholeskyQR2 Gram, SVD refinement) run on the */
-                          /*   tensor cores as exact BF16 digit products       */
-                          /*   (Ozaki splitting, see svlcov_dgemm): 0 default  */
-                          /*   (on), < 0 on the FP64 pipe.  Other modes: unused */
+  int32_t tensor_gemm;    /* SVLCOV_SMALL_MIXED: > 0 runs its FP64 small       */
+                          /*   products (folds, C0, CholeskyQR2 Gram, SVD       */
+                          /*   refinement) on the tensor cores as exact BF16    */
+                          /*   digit products (Ozaki splitting, see            */
+                          /*   svlcov_dgemm); <= 0 (default) on the FP64 pipe,  */
+                          /*   faster at the sizes of one step today (the digit */
+                          /*   split of each operand, not the MMAs, bounds the  */
+                          /*   tensor engine).  Other modes: unused             */
+  int32_t s1_secular;     /* FP64 and MIXED small modes, steps of one vector   */
+                          /*   (s = 1): SVD_k of K = [[Sigma, c], [0, rho]]     */
+                          /*   from the secular equation of the rank-one change */
+                          /*   K K^T = diag(Sigma^2, 0) + z z^T and Algorithm 2 */
+                          /*   as one normalisation: 0 default (on), < 0 the    */
+                          /*   general path (CholeskyQR2 and Jacobi)            */
 } svlcov_init_desc;
 
 /* One item of a batched run: kind 0 = add columns (a), 1 = add rows (a),
@@ -344,6 +353,22 @@ int svlcov_dgemm(int32_t ta, int32_t tb, int32_t M, int32_t N, int32_t K, double
 size_t svlcov_small_svd_work_bytes(int32_t n);
 int svlcov_small_svd(const double* K, int32_t n, int32_t k, double* F, double* theta, double* G,
                      int32_t precision, void* work, int32_t* sweeps, void* stream);
+
+/* SVD_k of the Rayleigh-Ritz matrix of a one-vector step (s = 1; Algorithms
+ * 3 and 11): K = [[diag(sigma), c], [0, rho]], (k+1) x (k+1), k <=
+ * SVLCOV_MAX_K, sigma descending and >= 0.  Since K K^T = diag(sigma^2, 0) +
+ * z z^T with z = [c; rho], the values are the roots of the secular equation
+ * of this rank-one change (one warp per root, FP64) and the vectors follow
+ * from them in closed form with the z that the computed roots make exact
+ * (Loewner), which keeps them orthogonal; deflation handles negligible z_i
+ * and coinciding poles.  sigma, c (k), rho (1): device FP64.  F, G:
+ * (k+1) x k column-major, theta (k) descending: device FP64 outputs.  work:
+ * device scratch of svlcov_small_svd_arrow_work_bytes() bytes, 256-byte
+ * aligned.  This is the kernel one-vector steps of the FP64 and mixed small
+ * modes use (init option s1_secular).  Asynchronous on `stream`. */
+size_t svlcov_small_svd_arrow_work_bytes(void);
+int svlcov_small_svd_arrow(const double* sigma, const double* c, const double* rho, int32_t k, double* F,
+                           double* theta, double* G, void* work, void* stream);
 
 /* The same rank-k small SVD for callers that cannot allocate device memory
  * (for example code running under another component's caching allocator,

@@ -39,7 +39,8 @@ class svlcov_init_desc(C.Structure):
                 ("ubuf", C.c_void_p), ("vbuf", C.c_void_p),
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
                 ("tau", C.c_double), ("reset_threshold", C.c_double), ("jacobi_block", C.c_int32),
-                ("reorth", C.c_int32), ("gemm_split", C.c_int32), ("tensor_gemm", C.c_int32)]
+                ("reorth", C.c_int32), ("gemm_split", C.c_int32), ("tensor_gemm", C.c_int32),
+                ("s1_secular", C.c_int32)]
 
 
 class svlcov_op(C.Structure):
@@ -91,6 +92,9 @@ SIGNATURES = {
     "svlcov_small_svd_work_bytes": (C.c_size_t, [C.c_int32]),
     "svlcov_small_svd": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+    "svlcov_small_svd_arrow_work_bytes": (C.c_size_t, []),
+    "svlcov_small_svd_arrow": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int32, C.c_void_p, C.c_void_p,
+                                         C.c_void_p, C.c_void_p, C.c_void_p]),
     "svlcov_dgemm": (C.c_int, [C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_int32, C.c_double, C.c_void_p,
                                 C.c_int32, C.c_void_p, C.c_int32, C.c_double, C.c_void_p, C.c_int32, C.c_int32,
                                 C.c_void_p]),

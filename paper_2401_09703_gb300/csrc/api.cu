@@ -128,6 +128,7 @@ struct svlcov_handle {
   void* jwork;
   void* rwork;  // FP64 refinement scratch of the mixed SVD
   void* rowork = nullptr;  // re-orthonormalisation scratch (when enabled)
+  char* awork = nullptr;   // SVD_k of a one-vector step (secular equation), FP64 small modes
   // bookkeeping of the last step
   int last_op = -1, last_s = 0;
   int64_t steps = 0;  // steps enqueued (schedules the re-orthonormalisation)
@@ -136,12 +137,12 @@ struct svlcov_handle {
 // The handle's split-K setting for the FP64 products it enqueues (restored
 // on leaving the entry point).
 // The same scope sets where the handle's FP64 products run: on the tensor
-// cores (ozaki_gemm) for the mixed small-step mode unless the handle's
-// tensor_gemm option is negative, else on the FP64 pipe.
+// cores (ozaki_gemm) for the mixed small-step mode when the handle's
+// tensor_gemm option is positive, else on the FP64 pipe.
 struct SplitScope {
   explicit SplitScope(const svlcov_handle* h) {
     set_gemm_split(!h || h->d.gemm_split >= 0);
-    set_gemm_tc(h && h->d.small == SVLCOV_SMALL_MIXED && h->d.tensor_gemm >= 0);
+    set_gemm_tc(h && h->d.small == SVLCOV_SMALL_MIXED && h->d.tensor_gemm > 0);
   }
   ~SplitScope() {
     set_gemm_split(true);
@@ -226,6 +227,7 @@ static void layout(svlcov_handle* h, void* base, size_t* total) {
   h->jwork = c.take<char>(jacobi_work_bytes((int)n2));
   h->rwork = c.take<char>(d.small == SVLCOV_SMALL_MIXED ? refine_work_bytes((int)n2, (int)k) : 256);
   h->rowork = reorth_on(d) ? c.take<char>(reorth_work_bytes((int)k, std::max(d.max_m, d.max_n))) : nullptr;
+  h->awork = d.small != SVLCOV_SMALL_FP32 ? c.take<char>(arrow_work_bytes()) : nullptr;
   *total = (c.off + 255) & ~(size_t)255;
 }
 
@@ -242,6 +244,10 @@ static bool desc_ok(const svlcov_init_desc* d) {
 }
 
 static bool small_is_f32(const svlcov_handle* h) { return h->d.small == SVLCOV_SMALL_FP32; }
+
+// One-vector steps of the FP64 small modes take the secular-equation SVD_k
+// and the scalar CholeskyQR (unless the handle's s1_secular option is < 0).
+static bool s1_fast(const svlcov_handle* h) { return h->d.small != SVLCOV_SMALL_FP32 && h->d.s1_secular >= 0; }
 
 extern "C" size_t svlcov_workspace_bytes(const svlcov_init_desc* d) {
   if (!desc_ok(d)) return 0;
@@ -451,6 +457,14 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
   int k = h->k, s = b.rows;
   int* status = h->status;
   prepare_side<TS, TC>(h, b, d_len, Xp, W, sb, st);
+  if (s == 1 && s1_fast(h)) {
+    // one vector: Algorithm 2 is one normalisation, R = sqrt(S) with the
+    // deflation rule, X = 1 / R, C_Q = C0 X, in FP64 (one launch)
+    launch_s1_orth((const double*)sb.S, (const double*)sb.e2, (const double*)sb.C0, k, h->d.tau, (double*)sb.R,
+                   (double*)sb.X, (double*)sb.CQ, sb.defl1, sb.defl2, status, st);
+    h->prof.end(st);
+    return;
+  }
   TC *C0 = (TC*)sb.C0, *e2 = (TC*)sb.e2;
   TC *S = (TC*)sb.S, *L1 = (TC*)sb.L1, *Y1 = (TC*)sb.Y1, *T1 = (TC*)sb.T1, *S2 = (TC*)sb.S2;
   TC *L2 = (TC*)sb.L2, *Y2 = (TC*)sb.Y2, *R = (TC*)sb.R, *X = (TC*)sb.X, *CQ = (TC*)sb.CQ;
@@ -562,14 +576,20 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
   h->prof.begin(PH_SVD, st);
   launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
-  // Empty update vectors give zero columns of K: move them last so that the
-  // Jacobi's tournament skips them (exact: their right vectors are unit vectors
-  // with zero singular values), then put G's rows back in the batch order.
-  launch_active_columns(b.indptr, s, k, h->perm, h->nact, status, st);
-  launch_permute_cols<TC>(K, n2, k, h->perm, (TC*)h->K2, status, st);
-  int e = small_svd_step<TC>(h, (TC*)h->K2, n2, F, theta, (TC*)h->G2, st, h->nact);     // F, Theta, G = SVD_k(K)
-  if (e) return SVLCOV_ERR_CUDA;
-  launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);
+  if (s == 1 && s1_fast(h)) {
+    // K K^T = diag(S^2, 0) + z z^T with z = [C0; R]: the secular-equation SVD
+    launch_arrow_svd((const double*)h->sigma, (const double*)sb.C0, (const double*)sb.R, k, (double*)F,
+                     (double*)theta, (double*)G, h->awork, status, st);
+  } else {
+    // Empty update vectors give zero columns of K: move them last so that the
+    // Jacobi's tournament skips them (exact: their right vectors are unit vectors
+    // with zero singular values), then put G's rows back in the batch order.
+    launch_active_columns(b.indptr, s, k, h->perm, h->nact, status, st);
+    launch_permute_cols<TC>(K, n2, k, h->perm, (TC*)h->K2, status, st);
+    int e = small_svd_step<TC>(h, (TC*)h->K2, n2, F, theta, (TC*)h->G2, st, h->nact);   // F, Theta, G = SVD_k(K)
+    if (e) return SVLCOV_ERR_CUDA;
+    launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);
+  }
   h->prof.next(PH_FOLD, st);
   {
     SideFork fk(h, st);
@@ -1333,6 +1353,20 @@ extern "C" const char* svlcov_strerror(int32_t code) {
     case SVLCOV_DEV_TIMEOUT: return "bounded device wait expired";
     default: return "combination of device status bits";
   }
+}
+
+// ---- standalone one-vector SVD ---------------------------------------------------
+extern "C" size_t svlcov_small_svd_arrow_work_bytes(void) { return arrow_work_bytes() + 16; }
+
+extern "C" int svlcov_small_svd_arrow(const double* sigma, const double* c, const double* rho, int32_t k, double* F,
+                                      double* theta, double* G, void* work, void* stream) {
+  if (!sigma || !c || !rho || !F || !theta || !G || !work || k < 1 || k > SVLCOV_MAX_K) return SVLCOV_ERR_INVALID_ARG;
+  if (((uintptr_t)work & 255) != 0) return SVLCOV_ERR_INVALID_ARG;
+  cudaStream_t st = (cudaStream_t)stream;
+  int* status = (int*)((char*)work + arrow_work_bytes());
+  if (cudaMemsetAsync(status, 0, sizeof(int), st) != cudaSuccess) return SVLCOV_ERR_CUDA;
+  launch_arrow_svd(sigma, c, rho, k, F, theta, G, work, status, st);
+  return last_launch();
 }
 
 // ---- standalone dense product --------------------------------------------------

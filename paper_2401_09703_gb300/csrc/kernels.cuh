@@ -189,6 +189,16 @@ int launch_add_cols_backward(const svlcov_csr& E, int k, const BackwardInputs& i
                              const double* Upre_S, const double* Upre_nnz, const double* Ubar, const double* thbar,
                              double* dvalues, double gap, void* work, int* status, cudaStream_t st);
 
+// SVD_k of K = [[diag(sigma), c], [0, rho]] (a one-vector step) through the
+// secular equation of K K^T = diag(sigma^2, 0) + z z^T (csrc/arrow.cu).
+size_t arrow_work_bytes();
+void launch_arrow_svd(const double* sigma, const double* c, const double* rho, int k, double* F, double* theta,
+                      double* G, void* work, const int* status, cudaStream_t st);
+// Algorithm 2 for one vector: R = sqrt(S) unless S <= tau e2 (deflated: R = X
+// = 0), X = 1 / R, C_Q = C0 X.
+void launch_s1_orth(const double* S, const double* e2, const double* C0, int k, double tau, double* R, double* X,
+                    double* CQ, unsigned char* defl1, unsigned char* defl2, int* status, cudaStream_t st);
+
 // Return code of an entry point after its launches: SVLCOV_ERR_CUDA if a
 // launch error is pending on this host thread (cudaGetLastError, which also
 // clears it), else SVLCOV_OK.

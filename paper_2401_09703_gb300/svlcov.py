@@ -65,7 +65,7 @@ class SVLCOV:
     def __init__(self, U0: torch.Tensor, sigma0: torch.Tensor, V0: torch.Tensor, *, max_m: int, max_n: int,
                  max_s: int, max_nnz: int, storage: str = "fp32", small: str = "mixed", tau: float = 0.0,
                  reset_threshold: float = 0.0, jacobi_block: int = 0, reorth: int = 0, gemm_split: int = 0,
-                 tensor_gemm: int = 0, stream=None):
+                 tensor_gemm: int = 0, s1_secular: int = 0, stream=None):
         assert U0.is_cuda and V0.is_cuda and sigma0.is_cuda
         m, k = U0.shape
         n = V0.shape[0]
@@ -90,6 +90,7 @@ class SVLCOV:
         d.reorth = reorth
         d.gemm_split = gemm_split
         d.tensor_gemm = tensor_gemm
+        d.s1_secular = s1_secular
         nbytes = lib().svlcov_workspace_bytes(C.byref(d))
         if nbytes == 0:
             raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_workspace_bytes")
@@ -350,6 +351,24 @@ def dgemm(A: torch.Tensor, B: torch.Tensor, *, ta: bool = False, tb: bool = Fals
                              B.shape[1], beta, _ptr(Ct), M, {"fp64": 0, "tensor": 1}[engine], _stream(stream)),
           "svlcov_dgemm")
     return Ct.t()
+
+
+def small_svd_arrow(sigma: torch.Tensor, c: torch.Tensor, rho: float, stream=None):
+    """SVD_k of K = [[diag(sigma), c], [0, rho]] with the library's
+    secular-equation kernel (the one-vector step's SVD)."""
+    dev = sigma.device
+    k = sigma.numel()
+    s = sigma.to(torch.float64).contiguous()
+    cc = c.to(torch.float64).contiguous()
+    r = torch.tensor([float(rho)], dtype=torch.float64, device=dev)
+    F = torch.empty((k, k + 1), dtype=torch.float64, device=dev)
+    G = torch.empty((k, k + 1), dtype=torch.float64, device=dev)
+    th = torch.empty(k, dtype=torch.float64, device=dev)
+    work = torch.empty(lib().svlcov_small_svd_arrow_work_bytes() + 256, dtype=torch.uint8, device=dev)
+    wp = (work.data_ptr() + 255) & ~255
+    check(lib().svlcov_small_svd_arrow(_ptr(s), _ptr(cc), _ptr(r), k, _ptr(F), _ptr(th), _ptr(G), C.c_void_p(wp),
+                                       _stream(stream)), "svlcov_small_svd_arrow")
+    return F.t(), th, G.t()
 
 
 def small_svd(K: torch.Tensor, k: int, precision: str = "fp64", stream=None):

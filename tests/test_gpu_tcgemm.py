@@ -91,3 +91,17 @@ def test_tensor_dgemm_rejects_bad_sizes():
     assert L.svlcov_dgemm(0, 0, 5000, 4, 4, 1.0, None, 5000, None, 4, 0.0, None, 5000, 1, None) == \
         _abi.SVLCOV_ERR_INVALID_ARG
     assert L.svlcov_dgemm(0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 2, None) == _abi.SVLCOV_ERR_INVALID_ARG
+
+
+@pytest.mark.parametrize("seed", [1, 2])
+def test_mixed_trajectory_with_tensor_products(seed):
+    """A mixed-mode trajectory (all three step kinds) whose FP64 small
+    products run on the tensor cores (init option tensor_gemm = 1) matches
+    the FP64 oracle as the FP64-pipe products do."""
+    from tests.gpu_util import compare, run_gpu, run_oracle
+    from tests.test_gpu_parity import _mixed_problem
+    U, s, V, ops = _mixed_problem(seed)
+    g, code, Ug, sg, Vg = run_gpu(U, s, V, ops, storage="fp64", small="mixed", tensor_gemm=1)
+    assert code == 0
+    c = compare(Ug, sg, Vg, run_oracle(U, s, V, ops))
+    assert c["sigma"] < 1e-10 and c["sin_u"] < 1e-8 and c["sin_v"] < 1e-8, c
