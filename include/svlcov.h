@@ -311,6 +311,21 @@ int svlcov_profile_enable(svlcov_handle* h, int32_t enable);
 int svlcov_profile_read(svlcov_handle* h, double* ms, int64_t* calls, int32_t nphases, int32_t reset,
                         int64_t* svd_sweeps);
 
+/* Scores of index pairs for the downstream tasks (Section 4, task setup of
+ * link prediction and collaborative filtering): out[p] = U[rows[p]]^T Sigma
+ * V[cols[p]], entry (rows[p], cols[p]) of the maintained U Sigma V^T, and
+ * with `symmetric` nonzero (undirected graph) the larger of that and
+ * U[cols[p]]^T Sigma V[rows[p]].  Computed from the extended decomposition
+ * as U'[i] M V'[j]^T with M = U'' diag(Sigma) V''^T, without materialising
+ * U or V; arithmetic in FP32 for FP32 / BF16 storage, FP64 for FP64 storage.
+ * rows, cols: device int32, npairs each; out: device FP64, npairs.  A pair
+ * with an index out of range (rows[p] >= m or cols[p] >= n, both directions
+ * for `symmetric`) scores NaN and sets SVLCOV_DEV_BAD_CSR in the status word.
+ * Asynchronous on `stream`; uses the handle's step scratch, so it must not
+ * overlap a step of the same handle. */
+int svlcov_score_pairs(svlcov_handle* h, const int32_t* rows, const int32_t* cols, int64_t npairs, int32_t symmetric,
+                       double* out, void* stream);
+
 /* Process-wide number of kernels this library has launched so far. */
 uint64_t svlcov_kernel_launches(void);
 

@@ -17,6 +17,7 @@ Three independent FP64 implementations of one update step:
 
 ``checks`` holds the error measures used to compare results; ``backward``
 the reference gradient of one add-columns step (torch float64 autograd of
-the dense formulation, and finite differences of the sparse method).
+the dense formulation, and finite differences of the sparse method);
+``scoring`` the pair scores of the downstream tasks.
 """
-from . import dense, svlcov, checks  # noqa: F401
+from . import dense, svlcov, checks, scoring  # noqa: F401

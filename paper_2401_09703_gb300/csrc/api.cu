@@ -1171,6 +1171,37 @@ extern "C" int svlcov_query_rows(svlcov_handle* h, int32_t side, const int32_t* 
   return last_launch();
 }
 
+template <typename TC>
+static void score_dispatch(svlcov_handle* h, const int32_t* rows, const int32_t* cols, int64_t npairs, int symmetric,
+                           double* out, cudaStream_t st) {
+  const TC *Wu = (const TC*)h->Wu, *Wv = (const TC*)h->Wv, *sg = (const TC*)h->sigma;
+  double* Mw = (double*)h->Itmp;   // k x k; step scratch, free between steps
+  switch (h->d.storage) {
+    case SVLCOV_FP64:
+      launch_score_pairs<double, TC>((const double*)h->d.ubuf, (const double*)h->d.vbuf, h->m, h->n, h->k, Wu, Wv, sg,
+                                     rows, cols, npairs, symmetric, out, Mw, h->status, st);
+      break;
+    case SVLCOV_FP32:
+      launch_score_pairs<float, TC>((const float*)h->d.ubuf, (const float*)h->d.vbuf, h->m, h->n, h->k, Wu, Wv, sg,
+                                    rows, cols, npairs, symmetric, out, Mw, h->status, st);
+      break;
+    default:
+      launch_score_pairs<__nv_bfloat16, TC>((const __nv_bfloat16*)h->d.ubuf, (const __nv_bfloat16*)h->d.vbuf, h->m,
+                                            h->n, h->k, Wu, Wv, sg, rows, cols, npairs, symmetric, out, Mw,
+                                            h->status, st);
+  }
+}
+
+extern "C" int svlcov_score_pairs(svlcov_handle* h, const int32_t* rows, const int32_t* cols, int64_t npairs,
+                                  int32_t symmetric, double* out, void* stream) {
+  if (!h || npairs < 0 || (npairs > 0 && (!rows || !cols || !out))) return SVLCOV_ERR_INVALID_ARG;
+  if (npairs == 0) return SVLCOV_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  if (small_is_f32(h)) score_dispatch<float>(h, rows, cols, npairs, symmetric != 0, out, st);
+  else score_dispatch<double>(h, rows, cols, npairs, symmetric != 0, out, st);
+  return last_launch();
+}
+
 extern "C" int svlcov_get_shape(const svlcov_handle* h, int64_t* m, int64_t* n, int32_t* k) {
   if (!h) return SVLCOV_ERR_INVALID_ARG;
   if (m) *m = h->m;

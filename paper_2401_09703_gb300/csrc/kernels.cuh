@@ -199,6 +199,13 @@ void launch_arrow_svd(const double* sigma, const double* c, const double* rho, i
 void launch_s1_orth(const double* S, const double* e2, const double* C0, int k, double tau, double* R, double* X,
                     double* CQ, unsigned char* defl1, unsigned char* defl2, int* status, cudaStream_t st);
 
+// Scores U'[i] M V'[j]^T (M = W_U diag(sigma) W_V^T) of index pairs, the
+// larger of both directions when `symmetric` (csrc/score.cu).
+template <typename TS, typename TC>
+void launch_score_pairs(const TS* Up, const TS* Vp, int64_t m, int64_t n, int k, const TC* Wu, const TC* Wv,
+                        const TC* sigma, const int32_t* rows, const int32_t* cols, int64_t npairs, int symmetric,
+                        double* out, double* Mwork, int* status, cudaStream_t st);
+
 // Return code of an entry point after its launches: SVLCOV_ERR_CUDA if a
 // launch error is pending on this host thread (cudaGetLastError, which also
 // clears it), else SVLCOV_OK.

@@ -264,6 +264,17 @@ class SVLCOV:
         out["svd_sweeps"] = int(sw.value)
         return out
 
+    def score_pairs(self, rows: torch.Tensor, cols: torch.Tensor, symmetric: bool = False,
+                    stream=None) -> torch.Tensor:
+        """U[rows]^T Sigma V[cols] per pair (device FP64), the larger of both
+        directions when `symmetric` (undirected graphs)."""
+        r = rows.to(device=self.device, dtype=torch.int32).contiguous()
+        c = cols.to(device=self.device, dtype=torch.int32).contiguous()
+        out = torch.empty(r.numel(), dtype=torch.float64, device=self.device)
+        check(lib().svlcov_score_pairs(self.h, _ptr(r), _ptr(c), r.numel(), 1 if symmetric else 0, _ptr(out),
+                                       _stream(stream)), "svlcov_score_pairs")
+        return out
+
     def intermediate(self, which: int, side: int = 0, stream=None) -> np.ndarray:
         r, c = C.c_int32(), C.c_int32()
         check(lib().svlcov_get_intermediate(self.h, which, side, None, 0, C.byref(r), C.byref(c), _stream(stream)),

@@ -14,7 +14,7 @@ pytestmark = pytest.mark.gpu
 
 
 def _case(name, k, g):
-    sig = np.sort(g.uniform(1, 30, k))[::-1]
+    sig = np.sort(g.uniform(1, 30, k))[::-1].copy()
     c = g.standard_normal(k)
     rho = 2.0
     if name == "small_update":
