@@ -326,6 +326,21 @@ int svlcov_profile_read(svlcov_handle* h, double* ms, int64_t* calls, int32_t np
 int svlcov_score_pairs(svlcov_handle* h, const int32_t* rows, const int32_t* cols, int64_t npairs, int32_t symmetric,
                        double* out, void* stream);
 
+/* Projection of update vectors onto the current singular space without
+ * updating it (Lemma 1, the gather that turns a batch into SV-LCOV form):
+ * P = X'^T E^T and, if C0 is not NULL, C0 = X''^T P = X^T E^T, where side 0
+ * takes X = U (E: s x m, each row an update vector over the m rows of A, as
+ * for add_cols) and side 1 takes X = V (E: s x n, as for add_rows).  One
+ * launch serves any number of vectors, e.g. the look-ahead projection of
+ * many pending batches (X' changes between steps only at the rows a step
+ * scatters to) or folding new users / items into the current
+ * representation.  P, C0: device FP64, k x s column-major.  k must be a
+ * multiple of 4 (SVLCOV_ERR_INVALID_ARG otherwise).  An index out of range
+ * sets SVLCOV_DEV_BAD_CSR and is skipped.  Asynchronous on `stream`; C0 uses
+ * the handle's step scratch for FP32 handles, so it must not overlap a step
+ * of the same handle. */
+int svlcov_project(svlcov_handle* h, int32_t side, const svlcov_csr* E, double* P, double* C0, void* stream);
+
 /* Process-wide number of kernels this library has launched so far. */
 uint64_t svlcov_kernel_launches(void);
 

@@ -92,6 +92,7 @@ SIGNATURES = {
     "svlcov_small_svd_work_bytes": (C.c_size_t, [C.c_int32]),
     "svlcov_small_svd": (C.c_int, [C.c_void_p, C.c_int32, C.c_int32, C.c_void_p, C.c_void_p, C.c_void_p,
                                    C.c_int32, C.c_void_p, C.POINTER(C.c_int32), C.c_void_p]),
+    "svlcov_project": (C.c_int, [C.c_void_p, C.c_int32, C.POINTER(svlcov_csr), C.c_void_p, C.c_void_p, C.c_void_p]),
     "svlcov_score_pairs": (C.c_int, [C.c_void_p, C.c_void_p, C.c_void_p, C.c_int64, C.c_int32, C.c_void_p,
                                      C.c_void_p]),
     "svlcov_small_svd_arrow_work_bytes": (C.c_size_t, []),

@@ -1202,6 +1202,32 @@ extern "C" int svlcov_score_pairs(svlcov_handle* h, const int32_t* rows, const i
   return last_launch();
 }
 
+extern "C" int svlcov_project(svlcov_handle* h, int32_t side, const svlcov_csr* E, double* P, double* C0,
+                              void* stream) {
+  if (!h || (side != 0 && side != 1) || !csr_ok(E) || (E->rows > 0 && !P)) return SVLCOV_ERR_INVALID_ARG;
+  if (E->cols != (side == 0 ? h->m : h->n) || (h->k & 3) != 0) return SVLCOV_ERR_INVALID_ARG;
+  if (E->rows == 0) return SVLCOV_OK;
+  cudaStream_t st = (cudaStream_t)stream;
+  const int64_t rows = side == 0 ? h->m : h->n;
+  const void* Xp = side == 0 ? h->d.ubuf : h->d.vbuf;
+  SplitScope split_scope(h);
+  switch (h->d.storage) {
+    case SVLCOV_FP64: launch_project<double, double>(*E, (const double*)Xp, rows, h->k, P, h->status, st); break;
+    case SVLCOV_FP32: launch_project<float, double>(*E, (const float*)Xp, rows, h->k, P, h->status, st); break;
+    default: launch_project<__nv_bfloat16, double>(*E, (const __nv_bfloat16*)Xp, rows, h->k, P, h->status, st);
+  }
+  if (C0) {   // C0 = W^T P with the side's small factor (FP64; FP32 handles widen it first)
+    const int k = h->k;
+    const double* W = (const double*)(side == 0 ? h->Wu : h->Wv);
+    if (small_is_f32(h)) {
+      launch_cast<float, double>((const float*)(side == 0 ? h->Wu : h->Wv), (double*)h->Itmp, (int64_t)k * k, st);
+      W = (const double*)h->Itmp;
+    }
+    gemm<double>(true, false, k, E->rows, k, 1.0, W, k, P, k, 0.0, C0, k, h->status, st);
+  }
+  return last_launch();
+}
+
 extern "C" int svlcov_get_shape(const svlcov_handle* h, int64_t* m, int64_t* n, int32_t* k) {
   if (!h) return SVLCOV_ERR_INVALID_ARG;
   if (m) *m = h->m;

@@ -57,18 +57,20 @@ struct ArrowWork {
   double rot_c[AR_MAXN], rot_s[AR_MAXN];
 };
 
-// f(tau) = 1 + sum_i z_i^2 / ((d_i - d_o) - tau) over the reduced poles, and
-// its derivative, by one warp; delta_i = d_i - d_o.
-__device__ __forceinline__ void secular(const ArrowWork& w, int o, double tau, int lane, double& f, double& df) {
+// At shift tau from pole o: the pole's own term -z_o^2 / tau, and the sum psi
+// of the other terms z_i^2 / ((d_i - d_o) - tau) with its derivative, by one
+// warp; f = 1 + psi - z_o^2 / tau is the secular function.
+__device__ __forceinline__ void secular(const ArrowWork& w, int o, double tau, int lane, double& psi, double& dpsi) {
   double s = 0.0, ds = 0.0;
   for (int i = lane; i < w.m; i += 32) {
+    if (i == o) continue;
     const double del = (w.d[i] - w.d[o]) - tau;
     const double q = w.z[i] / del;
     s = fma(q, w.z[i], s);     // z^2 / del
     ds = fma(q, q, ds);        // z^2 / del^2
   }
-  f = 1.0 + warp_sum(s);
-  df = warp_sum(ds);
+  psi = warp_sum(s);
+  dpsi = warp_sum(ds);
 }
 
 }  // namespace
@@ -89,20 +91,24 @@ __global__ void k_arrow_setup(const double* __restrict__ sigma, const double* __
     zn2 = fma(z[i], z[i], zn2);
     def[i] = 0;
   }
-  const double dmax = d[0] > 0.0 ? d[0] : 0.0;
-  const double tol = 8.0 * AR_EPS * fmax(dmax, zn2);
+  // Deflation in the scale of K (so that it perturbs K, not only K K^T, by at
+  // most the tolerance): z_i with |z_i| <= tol, and poles whose singular
+  // values differ by at most tol, are treated as exact deflations.
   const double zn = sqrt(zn2);
+  const double s1 = k > 0 ? fmax(sigma[0], 0.0) : 0.0;
+  const double tol = 8.0 * AR_EPS * fmax(s1, zn);
   for (int i = 0; i < n; ++i)
-    if (!(fabs(z[i]) * zn > tol)) def[i] = 1;       // also z = 0 overall
+    if (!(fabs(z[i]) > tol)) def[i] = 1;       // also z = 0 overall
   // Close poles, in order: the previous kept index p and the next kept i.  d is
   // descending (sigma descending, the new direction's pole 0 last).
   int nrot = 0;
   int p = -1;
   for (int i = 0; i < n; ++i) {
     if (def[i]) continue;
-    if (p >= 0 && d[p] - d[i] <= tol) {
+    const double sp = p >= 0 ? sigma[p] : 0.0, si = i < k ? sigma[i] : 0.0;
+    if (p >= 0 && sp - si <= tol) {
       // rotate in the (p, i) plane so that z_i takes the norm and z_p = 0:
-      // the rotation moves D by at most (d_p - d_i) |cs sn| <= tol
+      // the rotation moves K by at most (sigma_p - sigma_i) |cs sn| <= tol
       const double r = hypot(z[p], z[i]);
       const double cs = z[i] / r, sn = z[p] / r;
       w->rot_p[nrot] = p;
@@ -152,12 +158,13 @@ __global__ void __launch_bounds__(32) k_arrow_roots(ArrowWork* __restrict__ w, d
   zn2 = warp_sum(zn2);
   const double width = j == 0 ? zn2 : w->d[j - 1] - w->d[j];
   // which pole is the root closer to: the sign of f at the midpoint
-  double f, df;
+  double psi, dpsi;
   int o = j;
   double lo = 0.0, hi = width;          // tau bracket relative to pole o
   if (j > 0) {
-    secular(*w, j, 0.5 * width, lane, f, df);
-    if (f < 0.0) {                      // f increases on the interval: root above the midpoint
+    secular(*w, j, 0.5 * width, lane, psi, dpsi);
+    const double fm = 1.0 + psi - w->z[j] * w->z[j] / (0.5 * width);
+    if (fm < 0.0) {                     // f increases on the interval: root above the midpoint
       o = j - 1;                        // shift to the upper pole
       lo = -0.5 * width;
       hi = 0.0;
@@ -166,22 +173,34 @@ __global__ void __launch_bounds__(32) k_arrow_roots(ArrowWork* __restrict__ w, d
       hi = 0.5 * width;
     }
   }
-  // safeguarded Newton on f(tau) (f is increasing on the bracket): start at the
-  // end away from the shift pole
-  double t = o == j ? hi : lo;
-  if (j == 0) t = 0.5 * width;
-  for (int it = 0; it < 100; ++it) {
-    secular(*w, o, t, lane, f, df);
+  // Iteration exact in the pole's own term (Bunch, Nielsen & Sorensen's
+  // osculatory idea): psi is linearised around the current tau and
+  // 1 + psi + psi' (t - tau) - z_o^2 / t = 0 solved for t (the root of the
+  // right sign of a quadratic), safeguarded by the bracket [lo, hi].
+  const double zo2 = w->z[o] * w->z[o];
+  double t = 0.5 * (lo + hi);
+  for (int it = 0; it < 80; ++it) {
+    secular(*w, o, t, lane, psi, dpsi);
+    const double f = 1.0 + psi - zo2 / t;
     if (f == 0.0) break;
     if (f < 0.0) lo = t;
     else hi = t;
-    double tn = t - f / df;
-    if (!(tn > lo && tn < hi)) tn = 0.5 * (lo + hi);   // outside the bracket (or NaN): bisect
-    if (fabs(tn - t) <= 2.0 * AR_EPS * fabs(tn) || hi - lo <= 4.0 * AR_EPS * fmax(fabs(lo), fabs(hi))) {
-      t = tn;
-      break;
+    const double b = 1.0 + psi - dpsi * t;
+    double tn;
+    if (!(dpsi > 0.0)) tn = zo2 / b;
+    else {
+      const double disc = sqrt(fma(b, b, 4.0 * dpsi * zo2));
+      if (o == j)   // positive root
+        tn = b > 0.0 ? 2.0 * zo2 / (b + disc) : (disc - b) / (2.0 * dpsi);
+      else          // negative root
+        tn = b > 0.0 ? -(b + disc) / (2.0 * dpsi) : 2.0 * zo2 / (b - disc);
     }
+    if (fabs(tn - t) <= 4.0 * AR_EPS * fabs(t)) break;   // converged: the step is rounding (t stays)
+    // outside the bracket (or NaN): bisect; the first root may sit on its
+    // upper end d_0 + |z|^2 (a single non-deflated pole)
+    if (!(tn > lo && (tn < hi || (j == 0 && tn == hi)))) tn = 0.5 * (lo + hi);
     t = tn;
+    if (hi - lo <= 4.0 * AR_EPS * fmax(fabs(lo), fabs(hi))) break;
   }
   if (lane == 0) {
     w->tau[j] = t;

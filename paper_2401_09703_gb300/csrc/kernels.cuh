@@ -206,6 +206,11 @@ void launch_score_pairs(const TS* Up, const TS* Vp, int64_t m, int64_t n, int k,
                         const TC* sigma, const int32_t* rows, const int32_t* cols, int64_t npairs, int symmetric,
                         double* out, double* Mwork, int* status, cudaStream_t st);
 
+// P (k x s, column-major) = X'^T E^T for a batch E (s x rows), one warp per
+// update vector (csrc/project.cu); k a multiple of 4.
+template <typename TS, typename TP>
+void launch_project(const svlcov_csr& b, const TS* Xp, int64_t rows, int k, TP* P, int* status, cudaStream_t st);
+
 // Return code of an entry point after its launches: SVLCOV_ERR_CUDA if a
 // launch error is pending on this host thread (cudaGetLastError, which also
 // clears it), else SVLCOV_OK.

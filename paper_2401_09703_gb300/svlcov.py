@@ -264,6 +264,16 @@ class SVLCOV:
         out["svd_sweeps"] = int(sw.value)
         return out
 
+    def project(self, side: int, batch: "DeviceCSR", with_c0: bool = True, stream=None):
+        """P = X'^T E^T (k x s) and C0 = X^T E^T of update vectors (side 0:
+        columns over U's rows, side 1: rows over V's rows) without updating."""
+        k, s = self.k, batch.rows
+        P = torch.empty((s, k), dtype=torch.float64, device=self.device)     # column-major k x s
+        C0 = torch.empty((s, k), dtype=torch.float64, device=self.device) if with_c0 else None
+        check(lib().svlcov_project(self.h, side, C.byref(batch.c()), _ptr(P), _ptr(C0), _stream(stream)),
+              "svlcov_project")
+        return P.t(), (C0.t() if with_c0 else None)
+
     def score_pairs(self, rows: torch.Tensor, cols: torch.Tensor, symmetric: bool = False,
                     stream=None) -> torch.Tensor:
         """U[rows]^T Sigma V[cols] per pair (device FP64), the larger of both
