@@ -55,6 +55,7 @@ def parse():
     ap.add_argument("--s", type=int, default=256)
     ap.add_argument("--no-plain", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
+    ap.add_argument("--no-lookahead", action="store_true", help="skip the look-ahead projection measurement")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--jacobi-block", type=int, default=0,
                     help="columns per Jacobi block of the C2/streaming handles (0: the library default)")
@@ -348,6 +349,56 @@ def roofline_sparse(batches, k, b_f, prof, peak_gbs):
                 traffic=None, kernel="k_gather_gram + k_scatter + k_append (phases gather + apply)",
                 bytes_per_step=byts / max(len(batches) // 2, 1), ms_per_step=1e3 * t / max(len(batches) // 2, 1),
                 peak_note="measured copy bandwidth (MEASURED_PEAKS.json hbm_gbs)")
+
+
+LOOKAHEAD_WORKLOAD = ("look-ahead projection P = X'^T E^T of 64 pending batches of 1024 update vectors in one "
+                      "launch: X' = U' of the C3 rating-matrix shape (1,000,000 x k=128, > L2), Poisson(20) "
+                      "distinct uniform users per vector (1.31M nonzeros)")
+
+
+def lookahead_projection(torch, dev, peak_gbs, steps=10):
+    """The gather of the update step at HBM scale: svlcov_project over 65,536
+    pending update vectors against a 1M x 128 factor (BF16 and FP32 storage),
+    one launch per measurement, L2 flushed (512 MB write) before each.
+    Algorithmic bytes per launch: nnz (k b_f + 8) for the gathered rows and
+    the (index, value) pairs, 4 (s + 1) for the row pointers, and s k 8 for
+    the FP64 output P."""
+    from paper_2401_09703_gb300 import SVLCOV, DeviceCSR
+    E = synth.lookahead_batches()
+    n_users, k = E.cols, 128
+    dE = DeviceCSR.from_host(E.indptr, E.indices, E.values, E.rows, E.cols, device=dev, values_dtype=torch.float32)
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(1006)
+    U0 = torch.randn(n_users, k, device=dev, generator=gen) / np.sqrt(n_users)
+    V0 = torch.randn(4096, k, device=dev, generator=gen) / 64.0
+    sg = torch.linspace(10.0, 1.0, k, device=dev, dtype=torch.float64)
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device=dev)
+    out = {}
+    for storage, bf in (("bf16", 2), ("fp32", 4)):
+        h = SVLCOV(U0, sg, V0, max_m=n_users, max_n=4096, max_s=1, max_nnz=1, storage=storage, small="mixed",
+                   reorth=-1)
+        h.project(0, dE, with_c0=False)                 # warm-up
+        stream = torch.cuda.current_stream()
+        ms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            h.project(0, dE, with_c0=False)
+            e1.record(stream)
+            torch.cuda.synchronize()
+            ms.append(e0.elapsed_time(e1))
+        byts = E.nnz * (k * bf + 8) + 4 * (E.rows + 1) + E.rows * k * 8
+        t = float(np.median(ms)) / 1e3
+        achieved = byts / t / 1e9
+        out[storage] = dict(bound="hbm", achieved=round(achieved, 1), peak=peak_gbs, unit="GB/s",
+                            frac=round(achieved / peak_gbs, 4), traffic=None, kernel="k_project",
+                            bytes_per_launch=int(byts), ms_per_launch=round(t * 1e3, 4), nnz=int(E.nnz),
+                            vectors=int(E.rows), status=h.status())
+        del h
+    del U0, V0, flush
+    torch.cuda.empty_cache()
+    return dict(workload=LOOKAHEAD_WORKLOAD, l2="flushed (512 MB write) before each launch", **out)
 
 
 def measured_peaks():
@@ -886,6 +937,7 @@ def main():
         roof_hbm = roofline_sparse(p["batches"][2 * W:2 * (W + K)], args.k, 4, pr, peak_gbs)
         roof_hbm["peak_note"] += f" ({peak_kind})"
         cpu = None if args.no_cpu else cpu_baseline(p, args.cpu_seconds)
+        lookahead = None if args.no_lookahead else lookahead_projection(torch, dev, peak_gbs)
         phases = {k: dict(ms_total=round(v[0], 3), calls=v[1]) for k, v in prof["profile"].items()
                   if k != "svd_sweeps"}
         line = dict(
@@ -898,7 +950,7 @@ def main():
                                                        sigma_rel_err_vs_oracle=err["plain"], status=plain["status"]),
             sigma_rel_err_vs_oracle=err["mixed"], sigma_compared_after_node_batch=W + K,
             status=mixed["status"], resets=mixed["resets"],
-            roofline=roof, roofline_hbm=roof_hbm, phases_ms=phases, e2e=e2e, cpu_baseline=cpu,
+            roofline=roof, roofline_hbm=roof_hbm, roofline_lookahead=lookahead, phases_ms=phases, e2e=e2e, cpu_baseline=cpu,
             gpu_launches=int(mixed["launches"]), clocks=mixed["clocks"],
             wall_s_timed_region=mixed["wall"])
         print(json.dumps(line))

@@ -362,3 +362,20 @@ def c4_problem(seed: int = 1004, n_mats: int = 64, m_lo: int = 5_000, m_hi: int 
             batches.append(("weights", (D, E)))
         mats.append(dict(A=A, U=U, sigma=sig, V=V, k=k, m=m, n=n, batches=batches))
     return dict(name="C4", mats=mats)
+
+
+# ---------------------------------------------------------------------------
+def lookahead_batches(seed: int = 1006, n_users: int = 1_000_000, n_vectors: int = 65_536,
+                      mean_nnz: float = 20.0) -> CSR:
+    """Pending update vectors for the look-ahead projection: n_vectors new
+    item columns over n_users rows (the rating matrix of the C3 shape), each
+    with max(1, Poisson(mean_nnz)) distinct users drawn uniformly and
+    ratings 1..5, as one CSR of n_vectors rows (64 pending batches of 1024)."""
+    g = rng(seed)
+    cnt = np.maximum(1, g.poisson(mean_nnz, size=n_vectors))
+    r = np.repeat(np.arange(n_vectors, dtype=np.int64), cnt)
+    c = g.integers(0, n_users, size=r.size)
+    key = np.unique(r * n_users + c)                      # distinct users per vector
+    r, c = key // n_users, key % n_users
+    v = g.integers(1, 6, size=r.size).astype(np.float64)
+    return csr_from_coo(r, c, v, n_vectors, n_users)

@@ -19,7 +19,7 @@ def _case(name, k, g):
     rho = 2.0
     if name == "small_update":
         c, rho = c * 1e-9, 1e-9
-    elif name == "tie":
+    elif name == "tie" and k > 1:
         sig[k // 3] = sig[k // 3 + 1]
     elif name == "zero_c":
         c[k // 5] = 0.0
