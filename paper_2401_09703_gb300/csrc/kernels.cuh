@@ -211,6 +211,14 @@ void launch_score_pairs(const TS* Up, const TS* Vp, int64_t m, int64_t n, int k,
 template <typename TS, typename TP>
 void launch_project(const svlcov_csr& b, const TS* Xp, int64_t rows, int k, TP* P, int* status, cudaStream_t st);
 
+// out = X' W on the tensor cores (BF16 pieces, FP32 accumulation) for BF16 /
+// FP32 storage with k a multiple of 16 up to 128 (csrc/tcrowmul.cu); out may
+// be X' (the reset of the extended decomposition).
+bool rowmul_tc_ok(int storage_bytes, int k);
+template <typename TS, typename TC, typename TO>
+void launch_rowmul_tc(const TS* X, int64_t rows, int k, const TC* W, TO* out, const int* do_reset, const int* status,
+                      cudaStream_t st);
+
 // Return code of an entry point after its launches: SVLCOV_ERR_CUDA if a
 // launch error is pending on this host thread (cudaGetLastError, which also
 // clears it), else SVLCOV_OK.

@@ -458,6 +458,12 @@ template <typename TS, typename TC>
 void launch_reset(TS* Xp, int64_t rows, int k, const TC* Wn, const int* do_reset, const int* status,
                   cudaStream_t st) {
   if (rows <= 0) return;
+  if constexpr (sizeof(TS) != 8) {
+    if (rowmul_tc_ok((int)sizeof(TS), k)) {   // the dense fold X' <- X' W on the tensor cores
+      launch_rowmul_tc<TS, TC, TS>(Xp, rows, k, Wn, Xp, do_reset, status, st);
+      return;
+    }
+  }
   int nw = 8;
   size_t smem = sizeof(typename Acc<TS>::type) * ((size_t)k * k + nw * kMaxK);
   auto fn = k_rowmul<TS, TC, TS>;
@@ -471,6 +477,14 @@ template <typename TS, typename TC>
 void launch_materialize(const TS* Xp, int64_t rows, int64_t src_rows, int k, const TC* W, void* out,
                         int out_dtype, const int32_t* idx, cudaStream_t st, int* err) {
   if (rows <= 0) return;
+  if constexpr (sizeof(TS) != 8) {
+    if (!idx && rowmul_tc_ok((int)sizeof(TS), k)) {   // every row: U = U' W on the tensor cores
+      // as on the other path, a status bit set earlier (e.g. by a query) does not stop the write-out
+      if (out_dtype == SVLCOV_FP64) launch_rowmul_tc<TS, TC, double>(Xp, rows, k, W, (double*)out, nullptr, nullptr, st);
+      else launch_rowmul_tc<TS, TC, float>(Xp, rows, k, W, (float*)out, nullptr, nullptr, st);
+      return;
+    }
+  }
   int nw = 8;
   size_t smem = sizeof(typename Acc<TS>::type) * ((size_t)k * k + nw * kMaxK);
   int grid = (int)std::min<int64_t>(cdiv(rows, nw), 152 * 8);
