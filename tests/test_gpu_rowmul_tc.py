@@ -26,7 +26,7 @@ def test_materialise_matches_fp64_product(k, storage):
     s = np.sort(g0.uniform(1, 10, k))[::-1].copy()
     dev = torch.device("cuda")
     h = SVLCOV(torch.as_tensor(U, dtype=torch.float32, device=dev), torch.as_tensor(s, device=dev),
-               torch.as_tensor(V, dtype=torch.float32, device=dev), max_m=m + 8, max_n=n + 8, max_s=8, max_nnz=64,
+               torch.as_tensor(V, dtype=torch.float32, device=dev), max_m=m + 8, max_n=n + 32, max_s=8, max_nnz=64,
                storage=storage, small="mixed", reorth=-1)
     # a few column steps so that U'' is a general matrix
     for t in range(3):
@@ -43,7 +43,9 @@ def test_materialise_matches_fp64_product(k, storage):
     assert err < 4 * 2.0 ** -24, err
 
 
-@pytest.mark.parametrize("storage,stol,vtol", [("fp32", 1e-5, 1e-4), ("bf16", 1e-3, 1e-2)])
+# BF16: every reset rounds X' W to BF16 (relative 2^-9), so a reset on every
+# fold sits at the BF16 tolerances of the fuzz suite
+@pytest.mark.parametrize("storage,stol,vtol", [("fp32", 1e-5, 1e-4), ("bf16", 1e-2, 1e-1)])
 def test_forced_reset_k16_matches_oracle(storage, stol, vtol):
     U, s, V, ops = _mixed_problem(7, m=80, n=60, k=16)
     g, code, Ug, sg, Vg = run_gpu(U, s, V, ops, storage=storage, small="mixed", values_dtype=torch.float32,
