@@ -353,7 +353,8 @@ def roofline_sparse(batches, k, b_f, prof, peak_gbs):
 
 LOOKAHEAD_WORKLOAD = ("look-ahead projection P = X'^T E^T of 64 pending batches of 1024 update vectors in one "
                       "launch: X' = U' of the C3 rating-matrix shape (1,000,000 x k=128, > L2), Poisson(20) "
-                      "distinct uniform users per vector (1.31M nonzeros)")
+                      "distinct uniform users per vector (1.31M nonzeros); and the dense fold U = U' U'' of the "
+                      "same factor on the tensor cores")
 
 
 def lookahead_projection(torch, dev, peak_gbs, steps=10):
@@ -395,7 +396,31 @@ def lookahead_projection(torch, dev, peak_gbs, steps=10):
                             frac=round(achieved / peak_gbs, 4), traffic=None, kernel="k_project",
                             bytes_per_launch=int(byts), ms_per_launch=round(t * 1e3, 4), nnz=int(E.nnz),
                             vectors=int(E.rows), status=h.status())
-        del h
+        # the dense fold U = U' U'' of the whole factor (tensor cores), FP32 out:
+        # reads rows k b_f, writes rows k 4 bytes
+        Uo = torch.empty(n_users, k, dtype=torch.float32, device=dev)
+        from paper_2401_09703_gb300 import _abi
+        import ctypes as C
+        fold = lambda: _abi.check(_abi.lib().svlcov_get_factors(h.h, C.c_void_p(Uo.data_ptr()), None, None,  # noqa
+                                                                _abi.SVLCOV_FP32, C.c_void_p(stream.cuda_stream)),
+                                  "get_factors")
+        fold()
+        fms = []
+        for _ in range(steps):
+            flush.zero_()
+            e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            fold()
+            e1.record(stream)
+            torch.cuda.synchronize()
+            fms.append(e0.elapsed_time(e1))
+        fb = n_users * k * (bf + 4)
+        ft = float(np.median(fms)) / 1e3
+        out[storage + "_fold"] = dict(bound="hbm", achieved=round(fb / ft / 1e9, 1), peak=peak_gbs, unit="GB/s",
+                                      frac=round(fb / ft / 1e9 / peak_gbs, 4), kernel="k_rowmul_tc (U = U' U'')",
+                                      bytes_per_launch=int(fb), ms_per_launch=round(ft * 1e3, 4),
+                                      tensor_flops_per_launch=2 * n_users * k * k)
+        del h, Uo
     del U0, V0, flush
     torch.cuda.empty_cache()
     return dict(workload=LOOKAHEAD_WORKLOAD, l2="flushed (512 MB write) before each launch", **out)

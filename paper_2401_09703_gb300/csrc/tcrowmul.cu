@@ -10,10 +10,11 @@
 // Precision: FP32 results from BF16 pieces.  W (FP64 or FP32) is rounded to
 // FP32 and split exactly into three BF16 pieces W0 + W1 + W2 (8 significant
 // bits each); BF16 storage is one piece, FP32 storage three pieces X0 + X1 +
-// X2 the same way.  The products kept are those above 2^-24 relative
-// (X_a W_b with a + b <= 2: three MMAs per K-step for BF16 storage, six for
-// FP32), all accumulated in one FP32 accumulator; each piece product is exact
-// in FP32, so the result carries FP32 rounding only.
+// X2 the same way.  The products kept are those above 2^-32 relative
+// (X_a W_b with a + b <= 3: three MMAs per K-step for BF16 storage -- all of
+// them --, eight for FP32), all accumulated in one FP32 accumulator; each
+// piece product is exact in FP32, so the result carries the accumulator's
+// rounding only.
 //
 // Persistent CTAs (one per SM): W's pieces are staged once in shared memory
 // in the MMA's no-swizzle K-major layout; per 128-row tile the threads read
@@ -191,7 +192,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
 #pragma unroll
         for (int a = 0; a < NA; ++a)
 #pragma unroll
-          for (int b = 0; b + a <= 2; ++b) {
+          for (int b = 0; b < 3 && a + b <= 3; ++b) {
             const uint64_t ad = rdesc(a0 + a * planeA + ks * 2 * (RT_M * 16), RT_M * 16, 128);
             const uint64_t bd = rdesc(w0 + b * planeW + ks * 2 * (k * 16), k * 16, 128);
             const uint32_t acc = first ? 0u : 1u;
