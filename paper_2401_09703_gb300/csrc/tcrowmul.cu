@@ -17,13 +17,16 @@
 // rounding only.
 //
 // Persistent CTAs (one per SM): W's pieces are staged once in shared memory
-// in the MMA's no-swizzle K-major layout; per 128-row tile the threads read
-// the rows (32-byte vectors, coalesced), split them into the A pieces in
-// shared memory, one thread issues the MMAs, and after the commit the
-// accumulator is read back with tcgen05.ld and stored.  Rows of one tile are
-// read completely before any is written, and tiles are disjoint, so the
+// in the MMA's 128-byte-swizzled K-major layout; per 128-row tile each warp
+// reads whole rows (all its loads issued before any is used), splits them
+// into the A pieces in shared memory, one thread issues the MMAs, and after
+// the commit the accumulator is read back with tcgen05.ld, staged in shared
+// memory and written out as whole row segments (coalesced).  Rows of one tile
+// are read completely before any is written, and tiles are disjoint, so the
 // fold may run in place (out == X').
 #include <algorithm>
+#include <cstring>
+#include <type_traits>
 
 #include "kernels.cuh"
 
@@ -35,16 +38,6 @@ constexpr int RT_M = 128;          // rows per tile (MMA M, tensor-memory lanes)
 constexpr int RT_THREADS = 256;
 
 __device__ __forceinline__ uint32_t su32(const void* p) { return (uint32_t)__cvta_generic_to_shared(p); }
-
-// no-swizzle K-major matrix descriptor (version 1): start, leading byte
-// offset (next 8-element K chunk), stride byte offset (next 8-row group)
-__device__ __forceinline__ uint64_t rdesc(uint32_t saddr, uint32_t lbo, uint32_t sbo) {
-  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
-  d |= (uint64_t)((lbo >> 4) & 0x3FFFu) << 16;
-  d |= (uint64_t)((sbo >> 4) & 0x3FFFu) << 32;
-  d |= (uint64_t)1 << 46;
-  return d;
-}
 
 __device__ __forceinline__ bool rt_wait(uint32_t mbar, uint32_t phase) {
   for (long it = 0; it < (1L << 24); ++it) {
@@ -98,10 +91,29 @@ __device__ __forceinline__ void tmem_ld32x32(uint32_t taddr, float* v) {
 template <typename TS> struct APieces { static constexpr int n = 1; };
 template <> struct APieces<float> { static constexpr int n = 3; };
 
-// Shared layout of one operand piece with R rows and K = k columns: element
-// (r, c) at (c / 8) (R 16) + r 16 + (c % 8) 2 -- K chunks of 8 elements,
-// each a column of R / 8 core matrices (8 rows x 16 bytes, contiguous): the
-// leading byte offset is R 16, the stride byte offset 128.
+// Shared layout of every operand piece (A tile: 128 rows; W^T: k rows), K
+// padded to kp = a multiple of 64: the 128-byte-swizzled K-major layout of
+// the MMA -- K atoms of 64 elements, each holding its rows 128 bytes apart,
+// 8-row groups 1024 bytes apart, the 16-byte chunk c of row r stored at chunk
+// c ^ (r % 8).  A warp writing one row's 128 bytes touches every bank once.
+__device__ __forceinline__ uint32_t swz(int rows, int r, int c) {   // byte offset of element (r, c)
+  const int atom = c >> 6, w = c & 63;
+  return (uint32_t)(atom * rows * 128 + r * 128 + ((((w >> 3) ^ (r & 7)) << 4) | ((w & 7) << 1)));
+}
+
+// 128-byte-swizzle K-major descriptor: start, LBO 16 (unused for this
+// layout), SBO 1024 (8-row groups), version 1, layout type 2 (SWIZZLE_128B)
+__device__ __forceinline__ uint64_t sdesc128(uint32_t saddr) {
+  uint64_t d = (uint64_t)((saddr & 0x3FFFFu) >> 4);
+  d |= (uint64_t)1 << 16;
+  d |= (uint64_t)(1024 >> 4) << 32;
+  d |= (uint64_t)1 << 46;
+  d |= (uint64_t)2 << 61;
+  return d;
+}
+
+constexpr int RT_SLD = 33;   // staging row stride (floats): 32 columns + 1, conflict-free
+
 template <typename TS, typename TC, typename TO>
 __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_t rows, int k,
                                                              const TC* __restrict__ W, TO* out,
@@ -112,17 +124,19 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
   __shared__ uint32_t tmem_slot;
   if (do_reset && *(volatile const int*)do_reset == 0) return;
   if (status && failed(status)) return;
-  unsigned char* sm = (unsigned char*)(((uintptr_t)rt_raw + 127) & ~(uintptr_t)127);
-  const uint32_t planeA = (uint32_t)RT_M * k * 2, planeW = (uint32_t)k * k * 2;
-  unsigned char* Ap = sm;                       // NA pieces of the 128 x k tile
-  unsigned char* Wp = sm + (size_t)NA * planeA;  // 3 pieces of W^T (k x k, row n = column n of W)
-  const int tid = threadIdx.x, warp = tid >> 5;
-  // W^T pieces: element (n, c) = W(c, n) = W[n k + c]
-  for (int e = tid; e < k * k; e += blockDim.x) {
-    const int n = e / k, c = e - n * k;
-    uint16_t p0, p1, p2;
-    split3((float)W[(int64_t)n * k + c], p0, p1, p2);
-    const uint32_t off = (uint32_t)((c >> 3) * (k * 16) + n * 16 + (c & 7) * 2);
+  unsigned char* sm = (unsigned char*)(((uintptr_t)rt_raw + 1023) & ~(uintptr_t)1023);   // swizzle atoms: 1024-B aligned
+  const int kp = (k + 63) & ~63;
+  const uint32_t planeA = (uint32_t)RT_M * kp * 2, planeW = (uint32_t)k * kp * 2;
+  unsigned char* Ap = sm;                        // NA pieces of the 128 x kp tile
+  unsigned char* Wp = sm + (size_t)NA * planeA;   // 3 pieces of W^T (k x kp, row n = column n of W)
+  float* stg = (float*)(Wp + 3 * (size_t)planeW); // 2 x 128 x 33 FP32 staging of the output
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // W^T pieces: element (n, c) = W(c, n) = W[n k + c]; zero for c >= k
+  for (int e = tid; e < k * kp; e += blockDim.x) {
+    const int n = e / kp, c = e - n * kp;
+    uint16_t p0 = 0, p1 = 0, p2 = 0;
+    if (c < k) split3((float)W[(int64_t)n * k + c], p0, p1, p2);
+    const uint32_t off = swz(k, n, c);
     *(uint16_t*)(Wp + off) = p0;
     *(uint16_t*)(Wp + planeW + off) = p1;
     *(uint16_t*)(Wp + 2 * planeW + off) = p2;
@@ -146,39 +160,39 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
   const int64_t ntiles = cdiv(rows, RT_M);
   uint32_t phase = 0;
   bool ok = true;
+  constexpr int RPW = RT_M / (RT_THREADS / 32);   // rows per warp in the fill: 16
   for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int64_t r0 = tile * RT_M;
-    // ---- A pieces: item (row r, 32-byte segment q of the row)
-    constexpr int SEG = 32 / (int)sizeof(TS);       // elements per 32-byte segment: 16 BF16 or 8 FP32
-    const int nseg = k / SEG;
-    for (int it = tid; it < RT_M * nseg; it += blockDim.x) {
-      const int r = it % RT_M, q = it / RT_M;         // consecutive threads: consecutive rows
-      const int64_t gr = r0 + r;
-      uint4 v0 = make_uint4(0, 0, 0, 0), v1 = make_uint4(0, 0, 0, 0);
-      if (gr < rows) {
-        const uint4* src = (const uint4*)(X + gr * k + q * SEG);
-        v0 = src[0];
-        v1 = src[1];
+    // ---- A pieces: warp w fills rows w, w + 8, ...; lane l holds elements 4l .. 4l + 3
+    //      of a row (k <= 128); every load of the warp's 16 rows is issued first
+    {
+      const bool act = 4 * lane < k;
+      using VL = typename std::conditional<sizeof(TS) == 4, float4, uint2>::type;   // 4 elements
+      VL v[RPW];
+#pragma unroll
+      for (int i = 0; i < RPW; ++i) {
+        const int r = warp + 8 * i;
+        const int64_t gr = r0 + r;
+        if (act && gr < rows) v[i] = *reinterpret_cast<const VL*>(X + gr * k + 4 * lane);
+        else memset(&v[i], 0, sizeof(VL));
       }
-      if constexpr (NA == 1) {   // BF16: two 8-element chunks, copied as they are
-        const int c0 = q * 2;
-        *(uint4*)(Ap + (size_t)c0 * (RT_M * 16) + r * 16) = v0;
-        *(uint4*)(Ap + (size_t)(c0 + 1) * (RT_M * 16) + r * 16) = v1;
-      } else {                   // FP32: one 8-element chunk, three pieces
-        const float f[8] = {__uint_as_float(v0.x), __uint_as_float(v0.y), __uint_as_float(v0.z),
-                            __uint_as_float(v0.w), __uint_as_float(v1.x), __uint_as_float(v1.y),
-                            __uint_as_float(v1.z), __uint_as_float(v1.w)};
-        uint16_t p[3][8];
 #pragma unroll
-        for (int e = 0; e < 8; ++e) split3(f[e], p[0][e], p[1][e], p[2][e]);
+      for (int i = 0; i < RPW; ++i) {
+        const int r = warp + 8 * i;
+        if (4 * lane < kp) {
+          const uint32_t off = swz(RT_M, r, 4 * lane);
+          if constexpr (NA == 1) {
+            *(uint2*)(Ap + off) = *(const uint2*)&v[i];
+          } else {
+            const float* f = (const float*)&v[i];
+            uint16_t p[3][4];
 #pragma unroll
-        for (int a = 0; a < 3; ++a) {
-          uint4 w;
-          w.x = (uint32_t)p[a][0] | ((uint32_t)p[a][1] << 16);
-          w.y = (uint32_t)p[a][2] | ((uint32_t)p[a][3] << 16);
-          w.z = (uint32_t)p[a][4] | ((uint32_t)p[a][5] << 16);
-          w.w = (uint32_t)p[a][6] | ((uint32_t)p[a][7] << 16);
-          *(uint4*)(Ap + (size_t)a * planeA + (size_t)q * (RT_M * 16) + r * 16) = w;
+            for (int e = 0; e < 4; ++e) split3(f[e], p[0][e], p[1][e], p[2][e]);
+#pragma unroll
+            for (int a = 0; a < 3; ++a)
+              *(uint2*)(Ap + (size_t)a * planeA + off) =
+                  make_uint2((uint32_t)p[a][0] | ((uint32_t)p[a][1] << 16), (uint32_t)p[a][2] | ((uint32_t)p[a][3] << 16));
+          }
         }
       }
     }
@@ -188,13 +202,14 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
       const uint32_t a0 = su32(Ap), w0 = su32(Wp);
       bool first = true;
-      for (int ks = 0; ks < k / 16; ++ks) {
+      for (int ks = 0; ks < kp / 16; ++ks) {
+        const uint32_t koff = (uint32_t)((ks & 3) * 32);   // byte offset of the K-step inside its atom
 #pragma unroll
         for (int a = 0; a < NA; ++a)
 #pragma unroll
           for (int b = 0; b < 3 && a + b <= 3; ++b) {
-            const uint64_t ad = rdesc(a0 + a * planeA + ks * 2 * (RT_M * 16), RT_M * 16, 128);
-            const uint64_t bd = rdesc(w0 + b * planeW + ks * 2 * (k * 16), k * 16, 128);
+            const uint64_t ad = sdesc128(a0 + a * planeA + (ks >> 2) * (RT_M * 128) + koff);
+            const uint64_t bd = sdesc128(w0 + b * planeW + (ks >> 2) * (k * 128) + koff);
             const uint32_t acc = first ? 0u : 1u;
             asm volatile(
                 "{\n\t.reg .pred p;\n\t"
@@ -216,19 +231,31 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
       rt_wait(mb, phase ^ 1u);   // the MMAs in flight, bounded again
       break;
     }
-    // ---- epilogue: warp w reads lanes 32 (w % 4).. (rows), columns 32 (w / 4) + 64 j ..
+    // ---- epilogue, 64 columns per pass: warp w reads lanes 32 (w % 4) .. (rows) and
+    //      columns c0 + 32 (w / 4) .. into staging buffer w / 4; then every warp writes
+    //      whole row segments (coalesced)
     const int quad = warp & 3, half = warp >> 2;
-    const int r = 32 * quad + (tid & 31);
-    const int64_t gr = r0 + r;
-    for (int c0 = 32 * half; c0 < k; c0 += 64) {
-      float v[32];
-      tmem_ld32x32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)c0, v);
-      if (gr < rows) {   // X and out may be the same rows: every read of them came before the barrier
-        TO* dst = out + gr * k + c0;
+    for (int c0 = 0; c0 < k; c0 += 64) {
+      const int cc = c0 + 32 * half;
+      if (cc < k) {
+        float v[32];
+        tmem_ld32x32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cc, v);
+        float* sg = stg + (size_t)half * RT_M * RT_SLD + (32 * quad + lane) * RT_SLD;
 #pragma unroll
-        for (int j = 0; j < 32; ++j)
-          if (c0 + j < k) dst[j] = cvt_out<TO>(v[j]);
+        for (int j = 0; j < 32; ++j) sg[j] = v[j];
       }
+      __syncthreads();
+      const int ncol = min(64, k - c0);
+      for (int i = 0; i < RPW; ++i) {
+        const int r = warp + 8 * i;
+        const int64_t gr = r0 + r;
+        if (gr >= rows) continue;
+        for (int c = lane; c < ncol; c += 32) {
+          const float x = stg[(size_t)(c >> 5) * RT_M * RT_SLD + r * RT_SLD + (c & 31)];
+          out[gr * k + c0 + c] = cvt_out<TO>(x);
+        }
+      }
+      __syncthreads();
     }
     asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
     __syncthreads();   // the accumulator and the A pieces are free for the next tile
@@ -258,7 +285,9 @@ void launch_rowmul_tc(const TS* X, int64_t rows, int k, const TC* W, TO* out, co
     cudaDeviceGetAttribute(&g_rt_sms, cudaDevAttrMultiProcessorCount, dev);
     if (g_rt_sms <= 0) g_rt_sms = 152;
   }
-  const size_t smem = (size_t)APieces<TS>::n * RT_M * k * 2 + 3 * (size_t)k * k * 2 + 128;
+  const int kp = (k + 63) & ~63;
+  const size_t smem = (size_t)APieces<TS>::n * RT_M * kp * 2 + 3 * (size_t)k * kp * 2 +
+                      2 * (size_t)RT_M * RT_SLD * sizeof(float) + 1024;
   const uint32_t tcols = k <= 32 ? 32u : (k <= 64 ? 64u : 128u);
   auto fn = k_rowmul_tc<TS, TC, TO>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
