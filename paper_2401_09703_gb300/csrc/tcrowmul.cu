@@ -18,10 +18,11 @@
 //
 // Persistent CTAs (one per SM): W's pieces are staged once in shared memory
 // in the MMA's 128-byte-swizzled K-major layout; per 128-row tile each warp
-// reads whole rows (all its loads issued before any is used), splits them
-// into the A pieces in shared memory, one thread issues the MMAs, and after
-// the commit the accumulator is read back with tcgen05.ld, staged in shared
-// memory and written out as whole row segments (coalesced).  Rows of one tile
+// holds whole rows in registers (loaded while the previous tile was being
+// multiplied and written), splits them into the A pieces in shared memory,
+// one thread issues the MMAs, and after the commit the accumulator is read
+// back with tcgen05.ld, staged in shared memory and written out as whole row
+// segments (coalesced).  Rows of one tile
 // are read completely before any is written, and tiles are disjoint, so the
 // fold may run in place (out == X').
 #include <algorithm>
@@ -161,38 +162,41 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
   uint32_t phase = 0;
   bool ok = true;
   constexpr int RPW = RT_M / (RT_THREADS / 32);   // rows per warp in the fill: 16
+  // Rows of a tile: warp w loads rows w, w + 8, ... (lane l holds elements
+  // 4l .. 4l + 3, k <= 128).  The next tile's loads are issued right after the
+  // current tile's MMAs, so they are in flight during the MMAs and the
+  // epilogue (software pipelining across tiles).
+  using VL = typename std::conditional<sizeof(TS) == 4, float4, uint2>::type;   // 4 elements
+  const bool act = 4 * lane < k;
+  VL v[RPW];
+  auto load_tile = [&](int64_t tl) {
+#pragma unroll
+    for (int i = 0; i < RPW; ++i) {
+      const int64_t gr = tl * RT_M + warp + 8 * i;
+      if (act && gr < rows) v[i] = *reinterpret_cast<const VL*>(X + gr * k + 4 * lane);
+      else memset(&v[i], 0, sizeof(VL));
+    }
+  };
+  if ((int64_t)blockIdx.x < ntiles) load_tile(blockIdx.x);
   for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int64_t r0 = tile * RT_M;
-    // ---- A pieces: warp w fills rows w, w + 8, ...; lane l holds elements 4l .. 4l + 3
-    //      of a row (k <= 128); every load of the warp's 16 rows is issued first
-    {
-      const bool act = 4 * lane < k;
-      using VL = typename std::conditional<sizeof(TS) == 4, float4, uint2>::type;   // 4 elements
-      VL v[RPW];
+    // ---- A pieces from the rows already in registers
 #pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        const int r = warp + 8 * i;
-        const int64_t gr = r0 + r;
-        if (act && gr < rows) v[i] = *reinterpret_cast<const VL*>(X + gr * k + 4 * lane);
-        else memset(&v[i], 0, sizeof(VL));
-      }
+    for (int i = 0; i < RPW; ++i) {
+      const int r = warp + 8 * i;
+      if (4 * lane < kp) {
+        const uint32_t off = swz(RT_M, r, 4 * lane);
+        if constexpr (NA == 1) {
+          *(uint2*)(Ap + off) = *(const uint2*)&v[i];
+        } else {
+          const float* f = (const float*)&v[i];
+          uint16_t p[3][4];
 #pragma unroll
-      for (int i = 0; i < RPW; ++i) {
-        const int r = warp + 8 * i;
-        if (4 * lane < kp) {
-          const uint32_t off = swz(RT_M, r, 4 * lane);
-          if constexpr (NA == 1) {
-            *(uint2*)(Ap + off) = *(const uint2*)&v[i];
-          } else {
-            const float* f = (const float*)&v[i];
-            uint16_t p[3][4];
+          for (int e = 0; e < 4; ++e) split3(f[e], p[0][e], p[1][e], p[2][e]);
 #pragma unroll
-            for (int e = 0; e < 4; ++e) split3(f[e], p[0][e], p[1][e], p[2][e]);
-#pragma unroll
-            for (int a = 0; a < 3; ++a)
-              *(uint2*)(Ap + (size_t)a * planeA + off) =
-                  make_uint2((uint32_t)p[a][0] | ((uint32_t)p[a][1] << 16), (uint32_t)p[a][2] | ((uint32_t)p[a][3] << 16));
-          }
+          for (int a = 0; a < 3; ++a)
+            *(uint2*)(Ap + (size_t)a * planeA + off) =
+                make_uint2((uint32_t)p[a][0] | ((uint32_t)p[a][1] << 16), (uint32_t)p[a][2] | ((uint32_t)p[a][3] << 16));
         }
       }
     }
@@ -223,6 +227,9 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
       asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(mb)
                    : "memory");
     }
+    // the next tile's rows: in place (out == X) they are other rows than this
+    // tile's, so reading them before this tile is written is safe
+    if (tile + gridDim.x < ntiles) load_tile(tile + gridDim.x);
     ok = __syncthreads_and(rt_wait(mb, phase) ? 1 : 0) != 0;
     phase ^= 1u;
     asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
