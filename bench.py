@@ -46,10 +46,11 @@ def parse():
     ap.add_argument("--steps", type=int, default=0, help="timed node batches (0 = all after warm-up)")
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", default="gpu", choices=["gpu", "reference"])
-    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "stream"],
+    ap.add_argument("--workload", default="c2", choices=["c2", "c3", "c4", "c5", "stream", "lookahead"],
                     help="c2: graph node insertion (default, the headline); c3: ratings, k=128, s=1024, BF16 vs "
                          "FP32 factors; c4: 64 matrices, batched weight updates; c5: forward + backward of one "
-                         "differentiated column step; stream: single-node updates, plain vs CUDA graph")
+                         "differentiated column step; stream: single-node updates, plain vs CUDA graph; "
+                         "lookahead: the look-ahead projection and the tensor-core fold at 1M x 128 alone")
     ap.add_argument("--N", type=int, default=100_000)
     ap.add_argument("--k", type=int, default=64)
     ap.add_argument("--s", type=int, default=256)
@@ -914,6 +915,13 @@ def main():
         return main_c3(args)
     if args.workload == "stream":
         return main_stream(args)
+    if args.workload == "lookahead":
+        import torch
+        torch.cuda.set_device(0)
+        peak_gbs, peak_kind = measured_peaks()
+        res = lookahead_projection(torch, torch.device("cuda", 0), peak_gbs, steps=max(3, args.steps or 10))
+        print(json.dumps(dict(metric="look-ahead projection and tensor-core fold GB/s", peak_kind=peak_kind, **res)))
+        return 0
     import torch
     rank, world, local = dist_env()
     if world > 1:
