@@ -68,24 +68,18 @@ __device__ __forceinline__ void split3(float x, uint16_t& p0, uint16_t& p1, uint
   p2 = __bfloat16_as_ushort(b2);
 }
 
-template <typename TO> __device__ __forceinline__ TO cvt_out(float v);
-template <> __device__ __forceinline__ float cvt_out<float>(float v) { return v; }
-template <> __device__ __forceinline__ double cvt_out<double>(float v) { return (double)v; }
-template <> __device__ __forceinline__ __nv_bfloat16 cvt_out<__nv_bfloat16>(float v) { return __float2bfloat16_rn(v); }
-
-__device__ __forceinline__ void tmem_ld32x32(uint32_t taddr, float* v) {
-  uint32_t r[32];
+// 16 consecutive FP32 columns of this warp's 32 tensor-memory lanes.
+__device__ __forceinline__ void tmem_ld32x16(uint32_t taddr, float* v) {
+  uint32_t r[16];
   asm volatile(
-      "tcgen05.ld.sync.aligned.32x32b.x32.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
-      "%15, %16, %17, %18, %19, %20, %21, %22, %23, %24, %25, %26, %27, %28, %29, %30, %31}, [%32];"
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 {%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, "
+      "%15}, [%16];"
       : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]), "=r"(r[7]),
-        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15]),
-        "=r"(r[16]), "=r"(r[17]), "=r"(r[18]), "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]),
-        "=r"(r[24]), "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]), "=r"(r[31])
+        "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]), "=r"(r[14]), "=r"(r[15])
       : "r"(taddr));
   asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
 #pragma unroll
-  for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
+  for (int i = 0; i < 16; ++i) v[i] = __uint_as_float(r[i]);
 }
 
 // Pieces of the A operand: one for BF16 storage, three for FP32.
@@ -113,7 +107,18 @@ __device__ __forceinline__ uint64_t sdesc128(uint32_t saddr) {
   return d;
 }
 
-constexpr int RT_SLD = 33;   // staging row stride (floats): 32 columns + 1, conflict-free
+constexpr int RT_SLD = 36;   // staging row stride (floats): 32 columns + 4 (16-byte rows, 4 wavefronts per warp access)
+
+// four consecutive outputs from an FP32 quadruple
+__device__ __forceinline__ void store4(float* p, float4 x) { *(float4*)p = x; }
+__device__ __forceinline__ void store4(double* p, float4 x) {
+  ((double2*)p)[0] = make_double2(x.x, x.y);
+  ((double2*)p)[1] = make_double2(x.z, x.w);
+}
+__device__ __forceinline__ void store4(__nv_bfloat16* p, float4 x) {
+  const __nv_bfloat162 a = __floats2bfloat162_rn(x.x, x.y), b = __floats2bfloat162_rn(x.z, x.w);
+  *(uint2*)p = make_uint2(*(const uint32_t*)&a, *(const uint32_t*)&b);
+}
 
 template <typename TS, typename TC, typename TO>
 __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_t rows, int k,
@@ -130,7 +135,7 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
   const uint32_t planeA = (uint32_t)RT_M * kp * 2, planeW = (uint32_t)k * kp * 2;
   unsigned char* Ap = sm;                        // NA pieces of the 128 x kp tile
   unsigned char* Wp = sm + (size_t)NA * planeA;   // 3 pieces of W^T (k x kp, row n = column n of W)
-  float* stg = (float*)(Wp + 3 * (size_t)planeW); // 2 x 128 x 33 FP32 staging of the output
+  float* stg = (float*)(Wp + 3 * (size_t)planeW); // 128 x RT_SLD FP32 staging of the output
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
   // W^T pieces: element (n, c) = W(c, n) = W[n k + c]; zero for c >= k
   for (int e = tid; e < k * kp; e += blockDim.x) {
@@ -181,11 +186,12 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
   for (int64_t tile = blockIdx.x; tile < ntiles && ok; tile += gridDim.x) {
     const int64_t r0 = tile * RT_M;
     // ---- A pieces from the rows already in registers
+    // rows warp + 8 i share r % 8, so their swizzled offsets differ by 1024 i
+    const uint32_t off0 = swz(RT_M, warp, 4 * lane);
 #pragma unroll
     for (int i = 0; i < RPW; ++i) {
-      const int r = warp + 8 * i;
       if (4 * lane < kp) {
-        const uint32_t off = swz(RT_M, r, 4 * lane);
+        const uint32_t off = off0 + 1024u * (uint32_t)i;
         if constexpr (NA == 1) {
           *(uint2*)(Ap + off) = *(const uint2*)&v[i];
         } else {
@@ -238,28 +244,31 @@ __global__ void __launch_bounds__(RT_THREADS, 1) k_rowmul_tc(const TS* X, int64_
       rt_wait(mb, phase ^ 1u);   // the MMAs in flight, bounded again
       break;
     }
-    // ---- epilogue, 64 columns per pass: warp w reads lanes 32 (w % 4) .. (rows) and
-    //      columns c0 + 32 (w / 4) .. into staging buffer w / 4; then every warp writes
-    //      whole row segments (coalesced)
+    // ---- epilogue, 32 columns per pass: warp w reads TMEM lanes 32 (w % 4) .. (rows)
+    //      and 16 columns 16 (w / 4) .. of the pass into the staging tile (row-major,
+    //      stride RT_SLD floats); then the warps write whole row segments: lane l
+    //      takes row 4 i' + l / 8 of its rows and columns 4 (l % 8) .. + 3 (16-byte
+    //      shared reads, coalesced global writes of 128 B per row)
     const int quad = warp & 3, half = warp >> 2;
-    for (int c0 = 0; c0 < k; c0 += 64) {
-      const int cc = c0 + 32 * half;
+    for (int c0 = 0; c0 < k; c0 += 32) {
+      const int cc = c0 + 16 * half;
       if (cc < k) {
-        float v[32];
-        tmem_ld32x32(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cc, v);
-        float* sg = stg + (size_t)half * RT_M * RT_SLD + (32 * quad + lane) * RT_SLD;
+        float v[16];
+        tmem_ld32x16(tmem + ((uint32_t)(32 * quad) << 16) + (uint32_t)cc, v);
+        float* sg = stg + (32 * quad + lane) * RT_SLD + 16 * half;
 #pragma unroll
-        for (int j = 0; j < 32; ++j) sg[j] = v[j];
+        for (int j = 0; j < 4; ++j) *(float4*)(sg + 4 * j) = make_float4(v[4 * j], v[4 * j + 1], v[4 * j + 2], v[4 * j + 3]);
       }
       __syncthreads();
-      const int ncol = min(64, k - c0);
-      for (int i = 0; i < RPW; ++i) {
-        const int r = warp + 8 * i;
+      const int nq = min(32, k - c0) / 4;   // float4 columns in this pass
+      const int cq = lane & 7;
+#pragma unroll
+      for (int i = 0; i < RPW / 4; ++i) {
+        const int r = warp * RPW + 4 * i + (lane >> 3);
         const int64_t gr = r0 + r;
-        if (gr >= rows) continue;
-        for (int c = lane; c < ncol; c += 32) {
-          const float x = stg[(size_t)(c >> 5) * RT_M * RT_SLD + r * RT_SLD + (c & 31)];
-          out[gr * k + c0 + c] = cvt_out<TO>(x);
+        if (gr < rows && cq < nq) {
+          const float4 x = *(const float4*)(stg + r * RT_SLD + 4 * cq);
+          store4(out + gr * k + c0 + 4 * cq, x);
         }
       }
       __syncthreads();
@@ -294,7 +303,7 @@ void launch_rowmul_tc(const TS* X, int64_t rows, int k, const TC* W, TO* out, co
   }
   const int kp = (k + 63) & ~63;
   const size_t smem = (size_t)APieces<TS>::n * RT_M * kp * 2 + 3 * (size_t)k * kp * 2 +
-                      2 * (size_t)RT_M * RT_SLD * sizeof(float) + 1024;
+                      (size_t)RT_M * RT_SLD * sizeof(float) + 1024;
   const uint32_t tcols = k <= 32 ? 32u : (k <= 64 ? 64u : 128u);
   auto fn = k_rowmul_tc<TS, TC, TO>;
   cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
