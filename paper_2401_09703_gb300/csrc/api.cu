@@ -799,7 +799,7 @@ void approx_layout(void* base, int k, int s, int l, ApproxBufs& ab, size_t* tota
 // The l-vector basis of one projected side from its residual Gram sb.S:
 // GKL (Algorithm 9) or t RPI iterations (Algorithm 10) with an SV-LCOV QR
 // that is CholeskyQR2 on W^T S W (same R as Algorithm 2), pass-1 pivots
-// judged against the raw norms w^T S_E w (reading R8).
+// tested against the raw norms w^T S_E w (reading R8).
 template <typename TC>
 static void approx_basis(svlcov_handle* h, SideBufs& sb, int s, const svlcov_approx& a, ApproxSide& x,
                          cudaStream_t st) {

@@ -268,7 +268,7 @@ __global__ void __launch_bounds__(OZ_THREADS, 1) k_ozaki_gemm(OzParams p) {
   int issued = 0;   // chunks whose MMAs were committed to the mbarrier
   for (int c = 0; c < nchunks; ++c) {
     const int kc = kbeg + c * OZ_KC;
-    if (c > 0) {   // the previous chunk's MMAs have read the planes (uniform verdict)
+    if (c > 0) {   // the previous chunk's MMAs have read the planes (uniform outcome)
       ok = __syncthreads_and(mbar_wait(mb, (uint32_t)((c - 1) & 1)) ? 1 : 0) != 0;
       if (!ok) break;
       asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");

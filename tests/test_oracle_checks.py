@@ -211,11 +211,11 @@ def test_planted_sigma_mistake_fails_a_pin(wrong):
     assert any(abs(wrong(s, r) - e) > 1e-6 for s, r, e in cases)
 
 
-def test_planted_mistakes_change_a_parity_verdict():
+def test_planted_mistakes_change_a_parity_decision():
     """The rulers as a parity test uses them: a result whose leading block is
     rotated by 1e-3 out of the reference subspace must fail a 1e-4 subspace
     tolerance, and an exact result must pass; each planted ruler gets one of
-    the two verdicts wrong."""
+    the two decisions wrong."""
     rng = np.random.default_rng(11)
     n, k = 40, 6
     Ur, _ = np.linalg.qr(rng.standard_normal((n, k + 1)))
