@@ -92,6 +92,8 @@ void launch_build_L(const T* C0, const T* R, int k, int s, T* L, const int* stat
 template <typename T>
 void launch_add_diag(T* K, int n, const T* sigma, int k, const int* status, cudaStream_t st);
 size_t jacobi_work_bytes(int n);
+// FP32 sweeps by the Gram-form cluster kernel where it fits (default on).
+void set_jacobi_gram(bool on);
 int* jacobi_sweeps_ptr(void* work, int n, int elem);
 size_t refine_work_bytes(int n, int k);
 // n_active (optional, device): columns >= *n_active of K are zero; the
