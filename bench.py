@@ -752,7 +752,7 @@ def main_c5(args):
         h = SVLCOV(torch.as_tensor(p["U"], dtype=idt, device=dev),
                    torch.as_tensor(p["sigma"], device=dev), torch.as_tensor(p["V"], dtype=idt, device=dev),
                    max_m=N + 64, max_n=N + 64, max_s=max(b.rows, p["rows"].rows),
-                   max_nnz=max(b.nnz, p["rows"].nnz), storage=storage, small=small)
+                   max_nnz=max(b.nnz, p["rows"].nnz), storage=storage, small=small, literal_steps=1)
         h.add_rows(to_dev(p["rows"], torch.float32))
         state = h.get_state()
         S = torch.as_tensor(S_rows, dtype=torch.int32, device=dev)

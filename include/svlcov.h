@@ -129,6 +129,22 @@ typedef struct {
                           /*   K K^T = diag(Sigma^2, 0) + z z^T and Algorithm 2 */
                           /*   as one normalisation: 0 default (on), < 0 the    */
                           /*   general path (CholeskyQR2 and Jacobi)            */
+  int32_t literal_steps;  /* SVLCOV_SMALL_MIXED, add-columns / add-rows steps   */
+                          /*   of s > 1 vectors.  0 (default): the step forms   */
+                          /*   no R.  Since K G = F Theta, the folds of         */
+                          /*   Section 3.2 need only Sigma, G and Theta         */
+                          /*   (F[:k] - C_Q F[k:] = Sigma G[:k] Theta^-1,       */
+                          /*   R^-1 F[k:] = G[k:] Theta^-1), and K^T K =         */
+                          /*   [[Sigma^2, Sigma C0], [C0^T Sigma, E^T E]]       */
+                          /*   holds exactly (R^T R is the residual Gram), so   */
+                          /*   SVD_k runs FP32 sweeps on K with one FP32        */
+                          /*   Cholesky factor of the residual Gram in place of */
+                          /*   R and refines on K^T K in FP64; the second       */
+                          /*   CholeskyQR2 pass, R^-1 and C_Q are not formed.   */
+                          /*   > 0: the literal Algorithm 2 / 3 / 11 route      */
+                          /*   (R, X = R^-1, C_Q, K and F formed), which        */
+                          /*   svlcov_add_cols_backward and the R / K / F       */
+                          /*   intermediates need.  Other modes: unused         */
 } svlcov_init_desc;
 
 /* One item of a batched run: kind 0 = add columns (a), 1 = add rows (a),

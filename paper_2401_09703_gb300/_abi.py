@@ -40,7 +40,7 @@ class svlcov_init_desc(C.Structure):
                 ("workspace", C.c_void_p), ("workspace_bytes", C.c_size_t),
                 ("tau", C.c_double), ("reset_threshold", C.c_double), ("jacobi_block", C.c_int32),
                 ("reorth", C.c_int32), ("gemm_split", C.c_int32), ("tensor_gemm", C.c_int32),
-                ("s1_secular", C.c_int32)]
+                ("s1_secular", C.c_int32), ("literal_steps", C.c_int32)]
 
 
 class svlcov_op(C.Structure):

@@ -131,6 +131,7 @@ struct svlcov_handle {
   char* awork = nullptr;   // SVD_k of a one-vector step (secular equation), FP64 small modes
   // bookkeeping of the last step
   int last_op = -1, last_s = 0;
+  bool last_rfree = false;   // the last step formed no R, K or F (mixed R-free route)
   int64_t steps = 0;  // steps enqueued (schedules the re-orthonormalisation)
 };
 
@@ -248,6 +249,11 @@ static bool small_is_f32(const svlcov_handle* h) { return h->d.small == SVLCOV_S
 // One-vector steps of the FP64 small modes take the secular-equation SVD_k
 // and the scalar CholeskyQR (unless the handle's s1_secular option is < 0).
 static bool s1_fast(const svlcov_handle* h) { return h->d.small != SVLCOV_SMALL_FP32 && h->d.s1_secular >= 0; }
+// Add-columns / add-rows steps of the mixed mode that form no R (init option
+// literal_steps): every s except the one-vector secular path.
+static bool rfree(const svlcov_handle* h, int s) {
+  return h->d.small == SVLCOV_SMALL_MIXED && h->d.literal_steps <= 0 && !(s == 1 && s1_fast(h));
+}
 
 extern "C" size_t svlcov_workspace_bytes(const svlcov_init_desc* d) {
   if (!desc_ok(d)) return 0;
@@ -453,7 +459,7 @@ struct SideFork {
 
 template <typename TS, typename TC>
 static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, const TS* Xp, const TC* W, SideBufs& sb,
-                          cudaStream_t st) {
+                          cudaStream_t st, bool r_free = false) {
   int k = h->k, s = b.rows;
   int* status = h->status;
   prepare_side<TS, TC>(h, b, d_len, Xp, W, sb, st);
@@ -481,6 +487,10 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
     double tau1 = std::max(h->d.tau, 1e-6);
     launch_cholinv<float, double, false>(Sd, s, (const double*)e2, (float)tau1, (double*)L1, (double*)Y1, sb.defl1,
                                          (double*)S2, (double*)T1, status, st);
+    if (r_free) {   // L1 (S = L1 L1^T to FP32) is all an R-free add step needs
+      h->prof.end(st);
+      return;
+    }
     gemm<TC>(false, true, s, s, s, (TC)1, S, s, Y1, s, (TC)0, T1, s, status, st, TRI_B_UP);   // T1 = S Y1^T
     gemm<TC>(false, false, s, s, s, (TC)1, Y1, s, T1, s, (TC)0, S2, s, status, st, TRI_A_LO);  // S2 = Y1 S Y1^T
     launch_cholinv<float, double, true>((double*)S2, s, nullptr, (float)h->d.tau, (double*)L2, (double*)Y2,
@@ -534,6 +544,19 @@ static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
 
+// The same fold without R (mixed R-free steps): Xn = W diag(Sigma) G[:k]
+// Theta^-1 and Mt = (G[k:] Theta^-1 Xn^-1)^T, from K G = F Theta.
+static void fold_projected_rfree(svlcov_handle* h, SideBufs& sb, const double* W, const double* G, int s, double* Xtmp,
+                                 double* Wn, double* Winv, int* reset_flag, double* itmp, cudaStream_t st) {
+  int k = h->k;
+  int* status = h->status;
+  launch_rfree_fold_inputs((const double*)h->sigma, G, (const double*)h->theta, k, s, Xtmp, (double*)sb.Y, status,
+                           st);
+  gemm<double>(false, false, k, k, k, 1.0, W, k, Xtmp, k, 0.0, Wn, k, status, st);
+  launch_inverse<double>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp);
+  gemm<double>(true, true, k, s, k, 1.0, Winv, k, (double*)sb.Y, s, 0.0, (double*)sb.Mt, k, status, st);
+}
+
 // SVD_k of the Rayleigh-Ritz matrix: Jacobi in the small-step precision, or
 // FP32 sweeps + FP64 refinement in the mixed mode.
 template <typename TC>
@@ -572,15 +595,35 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
   int* rP = h->flags + (cols ? 0 : 1);
   int* rO = h->flags + (cols ? 1 : 0);
   int64_t rowsP = cols ? h->m : h->n, rowsO = cols ? h->n : h->m;
-  orthogonalise<TS, TC>(h, b, rowsP, XpP, WP, sb, st);
+  const bool rf = rfree(h, s);
+  orthogonalise<TS, TC>(h, b, rowsP, XpP, WP, sb, st, rf);
   TC *K = (TC*)h->K, *F = (TC*)h->F, *G = (TC*)h->G, *theta = (TC*)h->theta;
   h->prof.begin(PH_SVD, st);
-  launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
-  if (s == 1 && s1_fast(h)) {
+  if (rf) {
+    // R-free mixed step: FP32 sweeps on [[Sigma, C0], [0, L1^T]], FP64
+    // refinement on K^T K = [[Sigma^2, Sigma C0], [C0^T Sigma, S_E]] (held in
+    // the K buffer), both with the empty batch vectors' columns moved last.
+    launch_active_columns(b.indptr, s, k, h->perm, h->nact, status, st);
+    launch_build_K_chol((const double*)h->sigma, (const double*)sb.C0, (const double*)sb.L1, k, s, h->perm,
+                        (double*)h->K2, status, st);
+    launch_build_M((const double*)h->sigma, (const double*)sb.C0, (const double*)sb.SE, k, s, h->perm, (double*)K,
+                   status, st);
+    cudaEvent_t ja = nullptr, jb = nullptr;
+    if (h->prof.nested(PH_JACOBI, ja, jb)) set_jacobi_events(ja, jb);
+    const bool fk = t_side_fork && h->side_st;
+    int e = launch_mixed_svd_gram((const double*)h->K2, (const double*)K, n2, k, (double*)theta, (double*)h->G2,
+                                  h->jwork, h->rwork, status, st, h->stats, h->d.jacobi_block, h->nact,
+                                  fk ? h->side_st : nullptr, fk ? h->ev_fork : nullptr, fk ? h->ev_join : nullptr);
+    set_jacobi_events(nullptr, nullptr);
+    if (e) return SVLCOV_ERR_CUDA;
+    launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);
+  } else if (s == 1 && s1_fast(h)) {
+    launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
     // K K^T = diag(S^2, 0) + z z^T with z = [C0; R]: the secular-equation SVD
     launch_arrow_svd((const double*)h->sigma, (const double*)sb.C0, (const double*)sb.R, k, (double*)F,
                      (double*)theta, (double*)G, h->awork, status, st);
   } else {
+    launch_build_K_add<TC>((TC*)h->sigma, (TC*)sb.C0, (TC*)sb.R, k, s, K, status, st);    // K = [[S, C0],[0, R]]
     // Empty update vectors give zero columns of K: move them last so that the
     // Jacobi's tournament skips them (exact: their right vectors are unit vectors
     // with zero singular values), then put G's rows back in the batch order.
@@ -597,7 +640,11 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
     gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, so);      // W_O G[:k]
     launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, so, (TC*)h->Itmp2);
     gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, n2, (TC)0, (TC*)h->Nt, k, status, so);  // (G[k:] W_O^-1)^T
-    fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, (TC*)h->Itmp, st);
+    if (rf)
+      fold_projected_rfree(h, sb, (const double*)WP, (const double*)G, s, (double*)h->Xu, (double*)WPn,
+                           (double*)WPi, rP, (double*)h->Itmp, st);
+    else
+      fold_projected<TC>(h, sb, WP, F, n2, s, (TC*)h->Xu, WPn, WPi, rP, (TC*)h->Itmp, st);
   }
   FiniteSet<TC> fs{};
   fs.ptr[0] = theta; fs.count[0] = k;
@@ -710,6 +757,7 @@ static int do_add(svlcov_handle* h, const svlcov_csr* b, bool cols, void* stream
     else h->m += b->rows;
     h->last_op = cols ? 0 : 1;
     h->last_s = b->rows;
+    h->last_rfree = rfree(h, b->rows);
     ++h->steps;
   }
   return rc;
@@ -738,6 +786,7 @@ extern "C" int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, co
   if (rc == SVLCOV_OK) {
     h->last_op = 2;
     h->last_s = D_T->rows;
+    h->last_rfree = false;
     ++h->steps;
   }
   return rc;
@@ -1343,6 +1392,7 @@ extern "C" int svlcov_get_intermediate(svlcov_handle* h, int32_t which, int32_t 
                                        size_t capacity, int32_t* rows, int32_t* cols, void* stream) {
   if (!h || side < 0 || side > 1 || h->last_op < 0) return SVLCOV_ERR_INVALID_ARG;
   if (h->last_op > 2) return SVLCOV_ERR_STATE;   // approximate steps keep other intermediates
+  if (h->last_rfree && (which == 3 || which == 4 || which == 6)) return SVLCOV_ERR_STATE;   // R, K, F not formed
   int k = h->k, s = h->last_s, n2 = k + s;
   const SideBufs& sb = h->side[side];
   const double* src = nullptr;
@@ -1382,6 +1432,7 @@ extern "C" int svlcov_add_cols_backward(svlcov_handle* h, const svlcov_csr* E, c
   if (!h || !csr_ok(E) || !work) return SVLCOV_ERR_INVALID_ARG;
   if (h->d.small != SVLCOV_SMALL_FP64 && h->d.small != SVLCOV_SMALL_MIXED) return SVLCOV_ERR_INVALID_ARG;
   if (h->last_op != 0 || E->rows != h->last_s) return SVLCOV_ERR_STATE;
+  if (h->last_rfree) return SVLCOV_ERR_STATE;   // needs the literal route (init option literal_steps)
   if (nS < 0 || nS > h->m || (nS > 0 && (!rows_S || !U_pre_S || !dL_dU_S))) return SVLCOV_ERR_INVALID_ARG;
   if (E->nnz > 0 && (!U_pre_nnz || !dL_dvalues)) return SVLCOV_ERR_INVALID_ARG;
   const SideBufs& sb = h->side[0];

@@ -65,12 +65,13 @@ class SVLCOV:
     def __init__(self, U0: torch.Tensor, sigma0: torch.Tensor, V0: torch.Tensor, *, max_m: int, max_n: int,
                  max_s: int, max_nnz: int, storage: str = "fp32", small: str = "mixed", tau: float = 0.0,
                  reset_threshold: float = 0.0, jacobi_block: int = 0, reorth: int = 0, gemm_split: int = 0,
-                 tensor_gemm: int = 0, s1_secular: int = 0, stream=None):
+                 tensor_gemm: int = 0, s1_secular: int = 0, literal_steps: int = 0, stream=None):
         assert U0.is_cuda and V0.is_cuda and sigma0.is_cuda
         m, k = U0.shape
         n = V0.shape[0]
         dev = U0.device
         self.k, self.storage, self.small = int(k), storage, small
+        self.literal_steps = int(literal_steps)
         self.device = dev
         tdt = _TORCH_STORAGE[storage]
         self.ubuf = torch.empty((max_m, k), dtype=tdt, device=dev)
@@ -91,6 +92,7 @@ class SVLCOV:
         d.gemm_split = gemm_split
         d.tensor_gemm = tensor_gemm
         d.s1_secular = s1_secular
+        d.literal_steps = literal_steps
         nbytes = lib().svlcov_workspace_bytes(C.byref(d))
         if nbytes == 0:
             raise _abi.SvlcovError(_abi.SVLCOV_ERR_INVALID_ARG, "svlcov_workspace_bytes")
@@ -321,9 +323,13 @@ class _AddColsGrad(torch.autograd.Function):
 def add_cols_with_grad(model: SVLCOV, batch: DeviceCSR, rows_S: torch.Tensor, gap: float = 1e-6):
     """model.add_cols(batch), differentiable in batch.values: returns
     (U_new[rows_S] (FP64), Theta (FP64)).  rows_S: existing rows of U, strictly
-    ascending.  Needs small mode "fp64" or "mixed" and a batch without empty
+    ascending.  Needs small mode "fp64" or "mixed" (created with
+    literal_steps=1) and a batch without empty
     update vectors; after backward, model.status() reports SVLCOV_DEV_GAP_WARN
     if a singular-value pair fell under the gap guard."""
+    if model.small == "mixed" and model.literal_steps <= 0:
+        raise ValueError("add_cols_with_grad on a mixed handle needs literal_steps=1: the backward differentiates "
+                         "through R, R^-1 and F, which the default R-free mixed step does not form")
     rows_S = rows_S.to(device=model.device, dtype=torch.int32).contiguous()
     return _AddColsGrad.apply(batch.values, model, batch, rows_S, gap)
 

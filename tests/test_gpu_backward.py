@@ -53,7 +53,7 @@ def _gpu_model(U, sg, V, b, storage, small):
     dev = torch.device("cuda")
     return SVLCOV(torch.as_tensor(U, device=dev), torch.as_tensor(sg, device=dev), torch.as_tensor(V, device=dev),
                   max_m=U.shape[0] + 8, max_n=V.shape[0] + b.rows + 8, max_s=b.rows, max_nnz=b.nnz,
-                  storage=storage, small=small)
+                  storage=storage, small=small, literal_steps=1)
 
 
 def _gpu_grad(U, sg, V, b, S_rows, storage, small, gap=1e-6):

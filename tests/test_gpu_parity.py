@@ -173,22 +173,30 @@ def _small_c3(n_users=20000, n_items=5000, k=32, s=512, n_batches=2):
     return p["U"], p["sigma"], p["V"], p["batches"]
 
 
-@pytest.mark.parametrize("storage,small,tol", [("fp64", "fp64", 1e-10), ("fp64", "mixed", 1e-7),
-                                               ("fp32", "mixed", 1e-5), ("bf16", "mixed", 1e-3)])
-def test_c3_like_wide_batches(storage, small, tol):
+@pytest.mark.parametrize("storage,small,tol,literal", [("fp64", "fp64", 1e-10, 0), ("fp64", "mixed", 1e-7, 1),
+                                                       ("fp64", "mixed", 1e-7, 0), ("fp32", "mixed", 1e-5, 0),
+                                                       ("bf16", "mixed", 1e-3, 0)])
+def test_c3_like_wide_batches(storage, small, tol, literal):
     """Rating matrix (Zipf item popularity), users appended in batches of
     s = 512: wider than the one-CTA shared-memory Cholesky in FP64 and in the
     FP32 first pass, so the blocked factorization runs.  R of the first step
-    equals the oracle's (it is unique: positive diagonal)."""
+    equals the oracle's (it is unique: positive diagonal); a mixed step on the
+    default R-free route forms no R and says so."""
+    from paper_2401_09703_gb300 import SvlcovError
     U, s, V, ops = _small_c3()
     vdt = torch.float64 if storage == "fp64" else torch.float32
     idt = torch.float64 if storage == "fp64" else torch.float32
-    g = make_gpu(U, s, V, ops, storage=storage, small=small, init_dtype=idt)
+    g = make_gpu(U, s, V, ops, storage=storage, small=small, init_dtype=idt, literal_steps=literal)
     st = osv.State.init(U, s, V)
     for t, (kind, b) in enumerate(ops):
         g.apply(kind, dev_batch(kind, b, vdt))
         st.apply(kind, b)
         if t == 0 and storage == "fp64":
+            if small == "mixed" and not literal:
+                for which in (3, 4, 6):   # R, K, F
+                    with pytest.raises(SvlcovError):
+                        g.intermediate(which)
+                continue
             Rg, Ro = g.intermediate(3), st.log[-1]["R"]
             rtol = 1e-10 if small == "fp64" else 1e-7
             assert np.max(np.abs(Rg - Ro)) < rtol * np.abs(Ro).max()
@@ -198,6 +206,34 @@ def test_c3_like_wide_batches(storage, small, tol):
     assert c["sigma"] < tol, c
     stol = 1e-8 if tol < 1e-9 else 10 * tol
     assert c["sin_u"] < stol and c["sin_v"] < stol, c
+
+
+@pytest.mark.parametrize("storage", ["fp64", "fp32"])
+def test_rfree_and_literal_mixed_steps_agree(storage):
+    """The mixed step without R (folds from Sigma, G and Theta; SVD_k refined
+    on K^T K = [[Sigma^2, Sigma C0], [C0^T Sigma, E^T E]]) and the literal
+    Algorithm 2 / 3 / 11 step reach the same factors: both against the oracle
+    over a node-insertion trajectory (rows and columns steps, k = 16, s = 64),
+    and against each other."""
+    U, s, V, ops = _small_c2()
+    vdt = torch.float64 if storage == "fp64" else torch.float32
+    idt = torch.float64 if storage == "fp64" else torch.float32
+    st = osv.State.init(U, s, V)
+    for kind, b in ops:
+        st.apply(kind, b)
+    out = []
+    for literal in (0, 1):
+        g = make_gpu(U, s, V, ops, storage=storage, small="mixed", init_dtype=idt, literal_steps=literal)
+        for kind, b in ops:
+            g.apply(kind, dev_batch(kind, b, vdt))
+        assert g.status() == 0
+        out.append([x.cpu().numpy().astype(np.float64) for x in g.get_factors()])
+        c = compare(*out[-1], st)
+        tol = 1e-9 if storage == "fp64" else 1e-5
+        assert c["sigma"] < tol, (literal, c)
+        assert c["sin_u"] < 100 * tol and c["sin_v"] < 100 * tol, (literal, c)
+    (Ua, sa, Va), (Ub, sb, Vb) = out
+    assert np.max(np.abs(sa - sb)) / sa[0] < (1e-9 if storage == "fp64" else 1e-5)
 
 
 def test_reorthonormalisation_keeps_fp64_parity():
