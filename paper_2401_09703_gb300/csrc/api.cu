@@ -486,7 +486,7 @@ static void orthogonalise(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, 
     double* Sd = (double*)S;
     double tau1 = std::max(h->d.tau, 1e-6);
     launch_cholinv<float, double, false>(Sd, s, (const double*)e2, (float)tau1, (double*)L1, (double*)Y1, sb.defl1,
-                                         (double*)S2, (double*)T1, status, st);
+                                         (double*)S2, (double*)T1, status, st, r_free);
     if (r_free) {   // L1 (S = L1 L1^T to FP32) is all an R-free add step needs
       h->prof.end(st);
       return;

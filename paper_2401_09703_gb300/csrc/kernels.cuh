@@ -83,7 +83,7 @@ size_t cholinv_smem_bytes(int s, size_t elem);
 // with small A (the second CholeskyQR pass), factored in the delta form.
 template <typename T, typename SrcT, bool DELTA>
 void launch_cholinv(const SrcT* S, int s, const SrcT* ref, T tau, SrcT* L, SrcT* Y, unsigned char* defl,
-                    SrcT* Awork, SrcT* Twork, int* status, cudaStream_t st);
+                    SrcT* Awork, SrcT* Twork, int* status, cudaStream_t st, bool factor_only = false);
 template <typename T>
 void launch_build_K_add(const T* sigma, const T* C0, const T* R, int k, int s, T* K, const int* status,
                         cudaStream_t st);
