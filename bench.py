@@ -267,7 +267,7 @@ def run_e2e(p, batches, torch, dev, W, K):
     return dict(value=units / t, unit=UNIT, h2d_bytes_per_step=int(h2d / steps), d2h_bytes_per_step=8 * h.k)
 
 
-TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_jacobi_cluster_c2_n320_traffic.txt")
+TRAFFIC_RECORD = os.path.join(ROOT, "profiles", "k_jacobi_gram_c2_n320_traffic.txt")
 SVD_SOURCE = os.path.join(ROOT, "paper_2401_09703_gb300", "csrc", "dense.cu")
 FP32_ALU_PEAK_TFLOPS = 152 * 128 * 2 * 2.07e9 / 1e12    # 152 SMs x 128 FP32 lanes x 2 flop (FMA) x 2.07 GHz
 
@@ -322,7 +322,7 @@ def roofline_svd(p, prof, small, sweeps_per_launch, n):
     svd_ms, svd_calls = prof["svd"]
     return dict(bound="alu", achieved=round(achieved, 4), peak=round(FP32_ALU_PEAK_TFLOPS, 2), unit="TFLOP/s",
                 frac=round(achieved / FP32_ALU_PEAK_TFLOPS, 5), traffic=traffic, traffic_source=tnote,
-                kernel="k_jacobi_cluster (Rayleigh-Ritz SVD_k of K)", flops_per_launch=flops,
+                kernel="k_jacobi_gram (Rayleigh-Ritz SVD_k: FP32 sweeps)", flops_per_launch=flops,
                 flop_model="sweeps x 6 n^3", ms_per_launch=per_launch_s * 1e3,
                 svd_phase_ms_per_call=svd_ms / max(svd_calls, 1),
                 peak_note="FP32 ALU peak derived from 152 SMs x 128 lanes x 2 x 2.07 GHz (no measured ALU peak)")
