@@ -248,6 +248,10 @@ static bool small_is_f32(const svlcov_handle* h) { return h->d.small == SVLCOV_S
 
 // One-vector steps of the FP64 small modes take the secular-equation SVD_k
 // and the scalar CholeskyQR (unless the handle's s1_secular option is < 0).
+// FP64 Newton steps after the FP32 inverse of a guarded k x k factor (FP32 /
+// BF16 storage, cond_1 <= 1e2 / 1e1 by default): one leaves ~(thr eps32)^2,
+// below the rounding of the stored factors; FP64 storage keeps two.
+static int inv_newton(const svlcov_handle* h) { return h->d.storage == SVLCOV_FP64 ? 2 : 1; }
 static bool s1_fast(const svlcov_handle* h) { return h->d.small != SVLCOV_SMALL_FP32 && h->d.s1_secular >= 0; }
 // Add-columns / add-rows steps of the mixed mode that form no R (init option
 // literal_steps): every s except the one-vector secular path.
@@ -539,7 +543,8 @@ static void fold_projected(svlcov_handle* h, SideBufs& sb, const TC* W, const TC
   launch_copy2d<TC>(Fbig, n2, Xtmp, k, k, k, status, st);                                             // Fk
   gemm<TC>(false, false, k, k, s, (TC)-1, (TC*)sb.CQ, k, Fbig + k, n2, (TC)1, Xtmp, k, status, st);  // - C_Q Fs
   gemm<TC>(false, false, k, k, k, (TC)1, W, k, Xtmp, k, (TC)0, Wn, k, status, st);
-  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp,
+                    inv_newton(h));
   gemm<TC>(false, false, s, k, s, (TC)1, (TC*)sb.X, s, Fbig + k, n2, (TC)0, (TC*)sb.Y, s, status, st);
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
@@ -553,7 +558,8 @@ static void fold_projected_rfree(svlcov_handle* h, SideBufs& sb, const double* W
   launch_rfree_fold_inputs((const double*)h->sigma, G, (const double*)h->theta, k, s, Xtmp, (double*)sb.Y, status,
                            st);
   gemm<double>(false, false, k, k, k, 1.0, W, k, Xtmp, k, 0.0, Wn, k, status, st);
-  launch_inverse<double>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp);
+  launch_inverse<double>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp,
+                    inv_newton(h));
   gemm<double>(true, true, k, s, k, 1.0, Winv, k, (double*)sb.Y, s, 0.0, (double*)sb.Mt, k, status, st);
 }
 
@@ -638,7 +644,8 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
     SideFork fk(h, st);
     const cudaStream_t so = fk.stream();
     gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, n2, (TC)0, WOn, k, status, so);      // W_O G[:k]
-    launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, so, (TC*)h->Itmp2);
+    launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, so, (TC*)h->Itmp2,
+                      inv_newton(h));
     gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, n2, (TC)0, (TC*)h->Nt, k, status, so);  // (G[k:] W_O^-1)^T
     if (rf)
       fold_projected_rfree(h, sb, (const double*)WP, (const double*)G, s, (double*)h->Xu, (double*)WPn,
@@ -900,7 +907,8 @@ static void fold_projected_approx(svlcov_handle* h, SideBufs& sb, ApproxSide& x,
   launch_copy2d<TC>(Fbig, ldf, Xtmp, k, k, k, status, st);                                         // F[:k]
   gemm<TC>(false, false, k, k, l, (TC)-1, Cq, k, Fbig + k, ldf, (TC)1, Xtmp, k, status, st);        // - C' F[k:]
   gemm<TC>(false, false, k, k, k, (TC)1, Wx, k, Xtmp, k, (TC)0, Wn, k, status, st);
-  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp);
+  launch_inverse<TC>(Wn, k, Winv, h->d.reset_threshold, reset_flag, status, st, itmp,
+                    inv_newton(h));
   gemm<TC>(false, false, s, k, l, (TC)1, (TC*)x.W, s, Fbig + k, ldf, (TC)0, (TC*)sb.Y, s, status, st);  // W F[k:]
   gemm<TC>(true, true, k, s, k, (TC)1, Winv, k, (TC*)sb.Y, s, (TC)0, (TC*)sb.Mt, k, status, st);
 }
@@ -944,7 +952,8 @@ static int step_add_approx(svlcov_handle* h, const svlcov_csr& b, bool cols, con
     SideFork fk(h, st);
     const cudaStream_t so = fk.stream();
     gemm<TC>(false, false, k, k, k, (TC)1, WO, k, G, ns, (TC)0, WOn, k, status, so);      // W_O G[:k]
-    launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, so, (TC*)h->Itmp2);
+    launch_inverse<TC>(WOn, k, WOi, h->d.reset_threshold, rO, status, so, (TC*)h->Itmp2,
+                      inv_newton(h));
     gemm<TC>(true, true, k, s, k, (TC)1, WOi, k, G + k, ns, (TC)0, (TC*)h->Nt, k, status, so);  // (G[k:] W_O^-1)^T
     fold_projected_approx<TC>(h, sb, ab.side[0], WP, F, nl, s, l, (TC*)h->Xu, WPn, WPi, rP, (TC*)h->Itmp, st);
   }

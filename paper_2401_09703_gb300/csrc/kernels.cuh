@@ -137,7 +137,7 @@ void launch_unpermute_rows(const T* Gp, int n, int k, int cols, const int* perm,
 // Newton form used for FP64 W when thr <= 1e3.
 template <typename T>
 void launch_inverse(const T* W, int k, T* Winv, double thr, int* do_reset, int* status, cudaStream_t st,
-                    T* tmp = nullptr);
+                    T* tmp = nullptr, int newton = 2);
 template <typename T>
 void launch_copy(const T* src, T* dst, int64_t count, const int* status, cudaStream_t st);
 void launch_triu(double* A, int n, const int* status, cudaStream_t st);
