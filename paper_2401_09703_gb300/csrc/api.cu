@@ -625,7 +625,7 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
     int e = launch_mixed_svd_gram((const double*)h->K2, (const double*)K, n2, k, (double*)theta, (double*)h->G2,
                                   h->jwork, h->rwork, status, st, h->stats, h->d.jacobi_block, h->nact,
                                   fk ? h->side_st : nullptr, fk ? h->ev_fork : nullptr, fk ? h->ev_join : nullptr,
-                                  refine_iters(h));
+                                  refine_iters(h), h->d.storage == SVLCOV_FP64 ? 1e-3 : 3e-3);
     set_jacobi_events(nullptr, nullptr);
     if (e) return SVLCOV_ERR_CUDA;
     launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);

@@ -100,7 +100,7 @@ size_t refine_work_bytes(int n, int k);
 int launch_mixed_svd_gram(const double* Kc, const double* M, int n, int k, double* theta, double* G, void* jwork,
                           void* rwork, int* status, cudaStream_t st, int64_t* sweep_total, int bcap,
                           const int* n_active, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
-                          int iters);
+                          int iters, double stop_tol);
 void launch_build_K_chol(const double* sigma, const double* C0, const double* L, int k, int s, const int* perm,
                          double* Kp, const int* status, cudaStream_t st);
 void launch_build_M(const double* sigma, const double* C0, const double* SE, int k, int s, const int* perm,
