@@ -81,6 +81,8 @@ size_t cholinv_smem_bytes(int s, size_t elem);
 // the packed triangle fits, else blocked with GEMM panels and trailing
 // updates, using the scratch Awork and Twork (s x s each).  DELTA: S = I + A
 // with small A (the second CholeskyQR pass), factored in the delta form.
+// factor_only: L alone (Y not formed; where one CTA holds the triangle, only
+// the lower triangle of L is written).
 template <typename T, typename SrcT, bool DELTA>
 void launch_cholinv(const SrcT* S, int s, const SrcT* ref, T tau, SrcT* L, SrcT* Y, unsigned char* defl,
                     SrcT* Awork, SrcT* Twork, int* status, cudaStream_t st, bool factor_only = false);
