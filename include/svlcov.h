@@ -380,7 +380,12 @@ const char* svlcov_strerror(int32_t code);
  * tcgen05.mma in FP32 tensor memory, and the groups are summed in FP64;
  * accurate to ~2^-52 of max_k |a_ik| max_k |b_kj| per term (FP64 GEMM
  * accuracy), subnormal inputs read as zero, a non-finite input gives NaN in
- * its row / column.  M, N, K <= 4096.  Asynchronous on `stream`; returns
+ * its row / column.  engine 2: double-float on the FP32 pipe -- each operand
+ * split into FP32 hi + lo parts, the hi parts' products exact (product plus
+ * FMA error), the cross terms to FP32 rounding, TwoSum accumulation; accurate
+ * to a few 2^-44 of sum_k |a_ik b_kj| (the refinement products of steps whose
+ * factors are stored in FP32 / BF16); operands must lie in FP32 range.
+ * M, N, K <= 4096.  Asynchronous on `stream`; returns
  * SVLCOV_ERR_INVALID_ARG for bad sizes or pointers, SVLCOV_ERR_CUDA for a
  * launch error. */
 int svlcov_dgemm(int32_t ta, int32_t tb, int32_t M, int32_t N, int32_t K, double alpha, const double* A,

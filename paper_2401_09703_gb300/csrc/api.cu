@@ -437,7 +437,10 @@ static void prepare_side(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, c
   h->prof.next(PH_CHOLQR, st);
   TC* S = (TC*)sb.S;
   launch_copy<TC>(SE, S, (int64_t)s * s, status, st);
-  gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);        // S = S_E - C0^T C0
+  if (std::is_same<TC, double>::value && h->d.storage != SVLCOV_FP64 && s > 1)   // FP32 / BF16 factors: double-float suffices
+    gemm_df(true, false, s, s, k, -1.0, (const double*)C0, k, (const double*)C0, k, 1.0, (double*)S, s, status, st);
+  else
+    gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);      // S = S_E - C0^T C0
 }
 
 // Independent branches of a step (the two folds, the two sides of the apply
@@ -628,7 +631,7 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
     int e = launch_mixed_svd_gram((const double*)h->K2, (const double*)K, n2, k, (double*)theta, (double*)h->G2,
                                   h->jwork, h->rwork, status, st, h->stats, h->d.jacobi_block, h->nact,
                                   fk ? h->side_st : nullptr, fk ? h->ev_fork : nullptr, fk ? h->ev_join : nullptr,
-                                  refine_iters(h), sweep_stop(h));
+                                  refine_iters(h), sweep_stop(h), h->d.storage != SVLCOV_FP64);
     set_jacobi_events(nullptr, nullptr);
     if (e) return SVLCOV_ERR_CUDA;
     launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);
@@ -1499,12 +1502,16 @@ extern "C" int svlcov_small_svd_arrow(const double* sigma, const double* c, cons
 extern "C" int svlcov_dgemm(int32_t ta, int32_t tb, int32_t M, int32_t N, int32_t K, double alpha, const double* A,
                             int32_t lda, const double* B, int32_t ldb, double beta, double* C, int32_t ldc,
                             int32_t engine, void* stream) {
-  if (M < 0 || N < 0 || K < 0 || M > 4096 || N > 4096 || K > 4096 || (engine != 0 && engine != 1))
+  if (M < 0 || N < 0 || K < 0 || M > 4096 || N > 4096 || K > 4096 || engine < 0 || engine > 2)
     return SVLCOV_ERR_INVALID_ARG;
   if (M == 0 || N == 0) return SVLCOV_OK;
   if (!C || ldc < M || (K > 0 && (!A || !B))) return SVLCOV_ERR_INVALID_ARG;
   if (K > 0 && (lda < (ta ? K : M) || ldb < (tb ? N : K))) return SVLCOV_ERR_INVALID_ARG;
   cudaStream_t st = (cudaStream_t)stream;
+  if (engine == 2) {
+    gemm_df(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, st);
+    return last_launch();
+  }
   GemmTcScope tc(engine == 1);
   gemm<double>(ta != 0, tb != 0, M, N, K, alpha, A, lda, B, ldb, beta, C, ldc, nullptr, st);
   return last_launch();

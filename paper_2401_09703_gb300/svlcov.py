@@ -363,7 +363,8 @@ def dgemm(A: torch.Tensor, B: torch.Tensor, *, ta: bool = False, tb: bool = Fals
           beta: float = 0.0, C: torch.Tensor = None, engine: str = "tensor", stream=None) -> torch.Tensor:
     """alpha op(A) op(B) + beta C in FP64 with the library's product kernels
     (engine "tensor": BF16 digit products on the tensor cores; "fp64": the
-    FP64 pipe).  Tensors are device FP64 matrices in the usual row-major
+    FP64 pipe; "df32": double-float on the FP32 pipe, a few 2^-44 of
+    sum_k |a_ik b_kj|).  Tensors are device FP64 matrices in the usual row-major
     torch layout; they are handed to the column-major C call as transposes."""
     A = A.to(torch.float64).contiguous()
     B = B.to(torch.float64).contiguous()
@@ -375,7 +376,7 @@ def dgemm(A: torch.Tensor, B: torch.Tensor, *, ta: bool = False, tb: bool = Fals
     Ct = C.t().contiguous()                       # column-major M x N
     # row-major A (r x c) is column-major A^T: op(A) = A means the transpose flag set on the column-major view
     check(lib().svlcov_dgemm(0 if ta else 1, 0 if tb else 1, M, N, K, alpha, _ptr(A), A.shape[1], _ptr(B),
-                             B.shape[1], beta, _ptr(Ct), M, {"fp64": 0, "tensor": 1}[engine], _stream(stream)),
+                             B.shape[1], beta, _ptr(Ct), M, {"fp64": 0, "tensor": 1, "df32": 2}[engine], _stream(stream)),
           "svlcov_dgemm")
     return Ct.t()
 

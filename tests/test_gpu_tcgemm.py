@@ -90,7 +90,7 @@ def test_tensor_dgemm_rejects_bad_sizes():
     L = _abi.lib()
     assert L.svlcov_dgemm(0, 0, 5000, 4, 4, 1.0, None, 5000, None, 4, 0.0, None, 5000, 1, None) == \
         _abi.SVLCOV_ERR_INVALID_ARG
-    assert L.svlcov_dgemm(0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 2, None) == _abi.SVLCOV_ERR_INVALID_ARG
+    assert L.svlcov_dgemm(0, 0, 4, 4, 4, 1.0, None, 4, None, 4, 0.0, None, 4, 3, None) == _abi.SVLCOV_ERR_INVALID_ARG
 
 
 @pytest.mark.parametrize("seed", [1, 2])
