@@ -119,10 +119,12 @@ typedef struct {
                           /*   products (folds, C0, CholeskyQR2 Gram, SVD       */
                           /*   refinement) on the tensor cores as exact BF16    */
                           /*   digit products (Ozaki splitting, see            */
-                          /*   svlcov_dgemm); <= 0 (default) on the FP64 pipe,  */
-                          /*   faster at the sizes of one step today (the digit */
-                          /*   split of each operand, not the MMAs, bounds the  */
-                          /*   tensor engine).  Other modes: unused             */
+                          /*   svlcov_dgemm); 0 (default): in the update steps  */
+                          /*   of FP32 / BF16 factors in double-float on the    */
+                          /*   FP32 pipe (svlcov_dgemm engine 2, ~2^-44         */
+                          /*   relative, far below those factors' rounding),    */
+                          /*   else on the FP64 pipe; < 0: always on the FP64   */
+                          /*   pipe.  Other modes: unused                       */
   int32_t s1_secular;     /* FP64 and MIXED small modes, steps of one vector   */
                           /*   (s = 1): SVD_k of K = [[Sigma, c], [0, rho]]     */
                           /*   from the secular equation of the rank-one change */

@@ -140,14 +140,23 @@ struct svlcov_handle {
 // The same scope sets where the handle's FP64 products run: on the tensor
 // cores (ozaki_gemm) for the mixed small-step mode when the handle's
 // tensor_gemm option is positive, else on the FP64 pipe.
+// In the update steps (`step`) of that mode with the default tensor_gemm = 0
+// and factors stored in FP32 / BF16, they run in double-float on the FP32
+// pipe (gemm_df): ~2^-44 relative, far below the rounding of those factors --
+// the larger products of a lone handle, all of them for handles that run side
+// by side (gemm_split < 0), whose FP64 products fill the GPU.
 struct SplitScope {
-  explicit SplitScope(const svlcov_handle* h) {
+  explicit SplitScope(const svlcov_handle* h, bool step = false) {
     set_gemm_split(!h || h->d.gemm_split >= 0);
     set_gemm_tc(h && h->d.small == SVLCOV_SMALL_MIXED && h->d.tensor_gemm > 0);
+    const bool df = step && h && h->d.small == SVLCOV_SMALL_MIXED && h->d.tensor_gemm == 0 &&
+                    h->d.storage != SVLCOV_FP64;
+    set_gemm_df(!df ? 0 : h->d.gemm_split < 0 ? 2 : 1);
   }
   ~SplitScope() {
     set_gemm_split(true);
     set_gemm_tc(false);
+    set_gemm_df(0);
   }
 };
 
@@ -437,10 +446,7 @@ static void prepare_side(svlcov_handle* h, const svlcov_csr& b, int64_t d_len, c
   h->prof.next(PH_CHOLQR, st);
   TC* S = (TC*)sb.S;
   launch_copy<TC>(SE, S, (int64_t)s * s, status, st);
-  if (std::is_same<TC, double>::value && h->d.storage != SVLCOV_FP64 && s > 1)   // FP32 / BF16 factors: double-float suffices
-    gemm_df(true, false, s, s, k, -1.0, (const double*)C0, k, (const double*)C0, k, 1.0, (double*)S, s, status, st);
-  else
-    gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);      // S = S_E - C0^T C0
+  gemm<TC>(true, false, s, s, k, (TC)-1, C0, k, C0, k, (TC)1, S, s, status, st);        // S = S_E - C0^T C0
 }
 
 // Independent branches of a step (the two folds, the two sides of the apply
@@ -631,7 +637,7 @@ static int step_add(svlcov_handle* h, const svlcov_csr& b, bool cols, cudaStream
     int e = launch_mixed_svd_gram((const double*)h->K2, (const double*)K, n2, k, (double*)theta, (double*)h->G2,
                                   h->jwork, h->rwork, status, st, h->stats, h->d.jacobi_block, h->nact,
                                   fk ? h->side_st : nullptr, fk ? h->ev_fork : nullptr, fk ? h->ev_join : nullptr,
-                                  refine_iters(h), sweep_stop(h), h->d.storage != SVLCOV_FP64);
+                                  refine_iters(h), sweep_stop(h));
     set_jacobi_events(nullptr, nullptr);
     if (e) return SVLCOV_ERR_CUDA;
     launch_unpermute_rows<TC>((TC*)h->G2, n2, k, k, h->perm, G, status, st);
@@ -783,17 +789,17 @@ static int do_add(svlcov_handle* h, const svlcov_csr* b, bool cols, void* stream
 }
 
 extern "C" int svlcov_add_cols(svlcov_handle* h, const svlcov_csr* Ec_T, void* stream) {
-  SplitScope split_scope(h);
+  SplitScope split_scope(h, true);
   return do_add(h, Ec_T, true, stream);
 }
 
 extern "C" int svlcov_add_rows(svlcov_handle* h, const svlcov_csr* Er, void* stream) {
-  SplitScope split_scope(h);
+  SplitScope split_scope(h, true);
   return do_add(h, Er, false, stream);
 }
 
 extern "C" int svlcov_update_weights(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T, void* stream) {
-  SplitScope split_scope(h);
+  SplitScope split_scope(h, true);
   if (!h || !csr_ok(D_T) || !csr_ok(Em_T)) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->cols != h->m || Em_T->cols != h->n || D_T->rows != Em_T->rows) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->rows > h->d.max_s || D_T->nnz > h->d.max_nnz || Em_T->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;
@@ -1101,18 +1107,18 @@ static int do_add_approx(svlcov_handle* h, const svlcov_csr* b, bool cols, const
 
 extern "C" int svlcov_add_cols_approx(svlcov_handle* h, const svlcov_csr* Ec_T, const svlcov_approx* a,
                                       void* stream) {
-  SplitScope split_scope(h);
+  SplitScope split_scope(h, true);
   return do_add_approx(h, Ec_T, true, a, stream);
 }
 
 extern "C" int svlcov_add_rows_approx(svlcov_handle* h, const svlcov_csr* Er, const svlcov_approx* a, void* stream) {
-  SplitScope split_scope(h);
+  SplitScope split_scope(h, true);
   return do_add_approx(h, Er, false, a, stream);
 }
 
 extern "C" int svlcov_update_weights_approx(svlcov_handle* h, const svlcov_csr* D_T, const svlcov_csr* Em_T,
                                             const svlcov_approx* a, void* stream) {
-  SplitScope split_scope(h);
+  SplitScope split_scope(h, true);
   if (!h || !csr_ok(D_T) || !csr_ok(Em_T)) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->cols != h->m || Em_T->cols != h->n || D_T->rows != Em_T->rows) return SVLCOV_ERR_INVALID_ARG;
   if (D_T->rows > h->d.max_s || D_T->nnz > h->d.max_nnz || Em_T->nnz > h->d.max_nnz) return SVLCOV_ERR_CAPACITY;

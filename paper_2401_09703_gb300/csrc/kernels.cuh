@@ -64,9 +64,12 @@ enum { TRI_A_UP = 1, TRI_A_LO = 2, TRI_B_UP = 4, TRI_B_LO = 8 };
 // The FP64 product in double-float arithmetic on the FP32 pipe (operands
 // split into FP32 hi + lo, exact hi products, TwoSum accumulation): a few
 // 2^-44 of sum_k |a_ik b_kj|, for the refinement of FP32 / BF16 factors.
-// No triangular operand flags.
 void gemm_df(bool ta, bool tb, int M, int N, int Kd, double alpha, const double* A, int lda, const double* B, int ldb,
-             double beta, double* C, int ldc, const int* status, cudaStream_t st);
+             double beta, double* C, int ldc, const int* status, cudaStream_t st, int tri = 0);
+// Route this host thread's FP64 gemm calls to gemm_df (update steps of
+// mixed-mode handles with FP32 / BF16 factors): 0 never, 1 products of 2^21
+// multiply-adds and more, 2 all.
+void set_gemm_df(int mode);
 // The same FP64 product on the tensor cores: operands split into 7-bit BF16
 // digits (Ozaki), exact digit-pair products accumulated in FP32 tensor
 // memory by tcgen05.mma, summed in FP64 (csrc/tcgemm.cu).
@@ -108,7 +111,7 @@ size_t refine_work_bytes(int n, int k);
 int launch_mixed_svd_gram(const double* Kc, const double* M, int n, int k, double* theta, double* G, void* jwork,
                           void* rwork, int* status, cudaStream_t st, int64_t* sweep_total, int bcap,
                           const int* n_active, cudaStream_t side, cudaEvent_t ev_fork, cudaEvent_t ev_join,
-                          int iters, double stop_tol, bool df);
+                          int iters, double stop_tol);
 void launch_build_K_chol(const double* sigma, const double* C0, const double* L, int k, int s, const int* perm,
                          double* Kp, const int* status, cudaStream_t st);
 void launch_build_M(const double* sigma, const double* C0, const double* SE, int k, int s, const int* perm,
