@@ -71,6 +71,22 @@ def test_init_rejects_bad_arguments_without_cuda(lib):
     assert lib.svlcov_get_shape(None, None, None, None) == _abi.SVLCOV_ERR_INVALID_ARG
 
 
+def test_dgemm_engines_and_arguments_checked_without_cuda(lib):
+    """svlcov_dgemm's engines 0 (FP64 pipe), 1 (tensor cores) and 2
+    (double-float) share the host-side checks, which run before any CUDA call."""
+    from paper_2401_09703_gb300 import _abi
+    bad = _abi.SVLCOV_ERR_INVALID_ARG
+    dummy = C.c_void_p(16)   # never dereferenced: every call below returns before a launch
+    for engine in (-1, 3, 7):
+        assert lib.svlcov_dgemm(0, 0, 4, 4, 4, 1.0, dummy, 4, dummy, 4, 0.0, dummy, 4, engine, None) == bad
+    for engine in (0, 1, 2):
+        assert lib.svlcov_dgemm(0, 0, 4, 4, 4, 1.0, dummy, 4, dummy, 4, 0.0, None, 4, engine, None) == bad   # no C
+        assert lib.svlcov_dgemm(0, 0, 4, 4, 4, 1.0, dummy, 3, dummy, 4, 0.0, dummy, 4, engine, None) == bad  # lda < M
+        assert lib.svlcov_dgemm(1, 0, 4, 4, 5, 1.0, dummy, 4, dummy, 5, 0.0, dummy, 4, engine, None) == bad  # lda < K (A^T)
+        assert lib.svlcov_dgemm(0, 0, 4097, 4, 4, 1.0, dummy, 4097, dummy, 4, 0.0, dummy, 4097, engine, None) == bad
+        assert lib.svlcov_dgemm(0, 0, 0, 4, 4, 1.0, None, 1, None, 4, 0.0, None, 1, engine, None) == _abi.SVLCOV_OK
+
+
 def test_strerror(lib):
     assert lib.svlcov_strerror(0) == b"ok"
     assert b"CSR" in lib.svlcov_strerror(0x10)
